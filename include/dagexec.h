@@ -1,0 +1,273 @@
+/*
+ * dagexec.h -- C ABI of the fine-grained DAG executor for one GB300 (sm_103a).
+ *
+ * The library runs an application DAG G = <(K,B),(E_I,E_O,E)> (paper §3,
+ * "Problem Formulation": kernels K, buffers B = B_I u B_O, buffer->kernel
+ * edges E_I, kernel->buffer edges E_O, buffer->buffer edges E) of
+ * data-parallel kernels -- GEMM with fused bias/activation, row softmax and
+ * elementwise nodes -- with fine-grained concurrency: one persistent kernel
+ * pulls output tiles of all nodes from a device work queue and waits only on
+ * the producer tiles whose region it reads (tile-granularity dependency
+ * counters in HBM), so independent branches and the ready rows of dependent
+ * nodes overlap.  This is the sub-kernel, work-item-level interleaving of
+ * concurrent kernels that the paper names as its future work (§7,
+ * Conclusion); the coarse-grained alternative (§1: each kernel finished,
+ * with its copies, before its successors start) is kept as a baseline entry
+ * point (dag_submit_coarse).
+ *
+ * Conventions (all entry points):
+ *  - Plain C types only; a CUDA stream is passed as `void*` (a cudaStream_t,
+ *    NULL = the legacy default stream).
+ *  - The library owns all device memory: every buffer, the work queue, the
+ *    dependency counters and the trace.  The caller owns host pointers.
+ *  - Every function returns a dag_status; DAG_OK is 0.  On failure the
+ *    thread-local message of dag_last_error() says why.  No exception and no
+ *    abort crosses the ABI.
+ *  - A handle is not thread-safe: one host thread at a time per handle.
+ *  - After a device error (DAG_EDEVICE, DAG_ETIMEOUT from the device) the
+ *    handle is poisoned: every later call but dag_destroy returns the error.
+ */
+#ifndef DAGEXEC_H
+#define DAGEXEC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DAG_OK = 0,
+  DAG_EINVAL = 1,       /* bad argument, id out of range, edge list disagrees with the buffers */
+  DAG_ECYCLE = 2,       /* the kernel graph has a cycle (no valid schedule, Def. 5) */
+  DAG_ESHAPE = 3,       /* operand shapes disagree, or a view does not fit its parent */
+  DAG_EDTYPE = 4,       /* unsupported dtype combination (e.g. GEMM with mixed A/B dtypes) */
+  DAG_EMULTIWRITER = 5, /* a buffer element written by two kernels, or a kernel writing what it reads */
+  DAG_ENOMEM = 6,       /* device or host allocation failed */
+  DAG_EBUSY = 7,        /* a submit is still in flight on this handle */
+  DAG_ETIMEOUT = 8,     /* a device wait or dag_wait ran past its limit */
+  DAG_EDEVICE = 9,      /* a CUDA call failed */
+  DAG_EUNSUPPORTED = 10 /* shape/alignment the kernels do not handle */
+} dag_status;
+
+typedef enum { DAG_F32 = 0, DAG_BF16 = 1 } dag_dtype;
+
+/* Kernel kinds (paper §5 transformer head: GEMM, softmax; §2: vadd) */
+typedef enum { DAG_OP_GEMM = 0, DAG_OP_ADD = 1, DAG_OP_SOFTMAX = 2, DAG_OP_UNARY = 3 } dag_op;
+typedef enum { DAG_ACT_NONE = 0, DAG_ACT_RELU = 1, DAG_ACT_GELU = 2 } dag_act;
+
+/* buffer roles */
+#define DAG_BUF_INPUT 1u    /* contents come from the caller (an isolated write, §3) */
+#define DAG_BUF_OUTPUT 2u   /* read back by the caller (an isolated read, §3) */
+#define DAG_BUF_RESIDENT 4u /* with INPUT: uploaded once and kept (weights); no per-submit upload */
+
+/*
+ * A buffer b in B: a row-major rows x cols matrix.  The library picks the
+ * row pitch (a multiple of 16 elements).  view_of >= 0 makes this buffer a
+ * column slice [col_offset, col_offset+cols) of buffer view_of (same rows and
+ * dtype): a concat written in place by several kernels (§5, heads
+ * concatenated).  component: unused for buffers (keep 0).
+ */
+typedef struct {
+  int32_t rows, cols;
+  int32_t dtype;      /* dag_dtype */
+  uint32_t flags;     /* DAG_BUF_* */
+  int32_t view_of;    /* -1, or parent buffer id (the parent must not be a view) */
+  int32_t col_offset; /* first parent column of the slice */
+} dag_buffer_desc;
+
+/*
+ * A kernel k in K.  Inputs a, b, bias and output out are buffer ids; their
+ * roles define E_I (buffer -> kernel) and E_O (kernel -> buffer).
+ *   GEMM     out = act(scale * A.B + bias)  A: (batch*M) x K; B: (batch*K) x N,
+ *            or (batch*N) x K with trans_b = 1; bias: 1 x N or -1;
+ *            out: (batch*M) x N.  A and B share one dtype; f32 runs exact-f32
+ *            SIMT tiles, bf16 runs tensor-core tiles with f32 accumulation.
+ *   ADD      out = act(A + B), same shapes.
+ *   SOFTMAX  out[i,:] = softmax(scale * A[i,:]) (max-subtracted).
+ *   UNARY    out = act(A).
+ * component: task component id (paper §3, T in the partition of K); used by
+ *   dag_analyze for FRONT/END/IN and intra/inter edge classification; on one
+ *   GPU all components execute in the same persistent launch.
+ */
+typedef struct {
+  int32_t op;  /* dag_op */
+  int32_t a, b, bias, out;
+  int32_t trans_b;
+  int32_t act; /* dag_act */
+  float scale;
+  int32_t batch;
+  int32_t component;
+} dag_node_desc;
+
+/* An edge in the paper's form k_i,b_r -> k_j,b_s (§4.A): kernel src_node
+ * writes buffer src_buf, which kernel dst_node reads as dst_buf.  On one GPU
+ * the buffers of an intra edge are one object, so src_buf == dst_buf, or
+ * dst_buf is a view overlapping src_buf.  Edges are optional (they are implied
+ * by the buffer ids); when given, each must be implied (else DAG_EINVAL). */
+typedef struct {
+  int32_t src_node, src_buf, dst_node, dst_buf;
+} dag_edge;
+
+/* ready-queue ordering policies (paper §5: priority queue F ordered by the
+ * bottom-level rank; HEFT's rank from profiled times) */
+typedef enum {
+  DAG_SCHED_RANK_MODEL = 0,  /* bottom-level rank from a roofline time model */
+  DAG_SCHED_RANK_GIVEN = 1,  /* bottom-level rank from node_cost_us (measured profile or learned model) */
+  DAG_SCHED_FIFO = 2         /* tiles in topological node order, no ranking */
+} dag_sched;
+
+typedef struct {
+  uint64_t timeout_ns;        /* limit of every device spin-wait; 0 = 2 s */
+  int32_t trace;              /* record a per-tile trace (tickets, times, SM) */
+  int32_t max_ctas;           /* persistent grid size; 0 = one CTA per SM */
+  int32_t scheduler;          /* dag_sched */
+  int32_t tile_override;      /* 0 = automatic; else forces every bf16 GEMM to BN = tile_override (64/128/256) */
+  const float *node_cost_us;  /* per-node time estimates for DAG_SCHED_RANK_GIVEN (n_nodes entries) */
+  int32_t debug_never_ready;  /* test hook: >0 makes that many tiles wait on a counter nothing releases,
+                                 so the device wait runs out and reports DAG_ETIMEOUT */
+  int32_t reserved[7];
+} dag_options;
+
+typedef struct dag_handle dag_handle;
+
+/*
+ * dag_create: validate the DAG (acyclic, one writer per element, shapes and
+ * dtypes), tile every kernel, build the tile dependency counters, order the
+ * tiles (a linear extension of the tile DAG ranked by the scheduler), and
+ * allocate all device memory.  opts may be NULL.  *out receives the handle;
+ * free it with dag_destroy.  Needs a CUDA device.
+ */
+dag_status dag_create(const dag_node_desc *nodes, int n_nodes, const dag_edge *edges, int n_edges,
+                      const dag_buffer_desc *buffers, int n_buffers, const dag_options *opts,
+                      dag_handle **out);
+
+/*
+ * dag_set_input: give the host data of input buffer `buf` (rows x cols,
+ * dense, its dtype: f32 or bf16 bit patterns).  The pointer is recorded, not
+ * copied: it must stay valid and unchanged until the next dag_wait returns.
+ * The copy runs at the next dag_submit on an upload stream (a copy engine)
+ * that overlaps compute; tiles reading the buffer wait on its ready flag.
+ * Pinned memory (dag_host_alloc) makes the copy asynchronous.
+ */
+dag_status dag_set_input(dag_handle *h, int buf, const void *host_ptr);
+
+/* dag_set_output: host destination (rows x cols, dense) that every following
+ * dag_submit fills after the kernel (device->host on a copy stream); NULL
+ * cancels.  Same lifetime rule as dag_set_input. */
+dag_status dag_set_output(dag_handle *h, int buf, void *host_ptr);
+
+/*
+ * dag_submit: enqueue one execution: pending uploads on the upload streams
+ * (each followed by its ready flag), one persistent executor launch on
+ * `stream`, and registered readbacks.  Asynchronous; returns after enqueue.
+ * DAG_EBUSY if the previous submit was not waited for.
+ */
+dag_status dag_submit(dag_handle *h, void *stream);
+
+/* dag_submit_coarse: the coarse-grained baseline: uploads on `stream`, then
+ * one launch per kernel in topological order on `stream` (the same tile code,
+ * a grid of that kernel's tiles, no cross-kernel overlap), then readbacks. */
+dag_status dag_submit_coarse(dag_handle *h, void *stream);
+
+/* dag_wait: block until the last submit finished or timeout_ns passed
+ * (DAG_ETIMEOUT, the submit stays in flight).  Then reads the device error
+ * word: DAG_ETIMEOUT if a device wait ran out, DAG_EDEVICE on a CUDA error. */
+dag_status dag_wait(dag_handle *h, uint64_t timeout_ns);
+
+/* dag_get_output: synchronous device->host copy of buffer `buf` (rows x cols,
+ * dense) into host_ptr; call after dag_wait. */
+dag_status dag_get_output(dag_handle *h, int buf, void *host_ptr);
+
+/* dag_device_ptr: device address of buffer `buf` (borrowed, valid until
+ * dag_destroy) and its row pitch in elements; NULL on a bad id. */
+const void *dag_device_ptr(dag_handle *h, int buf, int64_t *ld_elems);
+
+/* dag_destroy: wait for outstanding work (bounded), free everything. */
+dag_status dag_destroy(dag_handle *h);
+
+/* dag_last_error: message of the last failure on this thread ("" if none). */
+const char *dag_last_error(void);
+
+/* pinned host memory for asynchronous uploads/readbacks */
+void *dag_host_alloc(size_t bytes);
+void dag_host_free(void *p);
+
+/* ------------------------------------------------------------------------ */
+/* Inspection                                                                */
+/* ------------------------------------------------------------------------ */
+
+/* Host-only analysis (no device needed), following §3 Defs. 1-3 and the
+ * classification of buffer edges and copies that follows them.  Per kernel:
+ * the bit set cls[k] (1 = FRONT(T), 2 = END(T), 4 = IN(T)) of its task
+ * component T.  Per E_I / E_O pair: isolated vs dependent copy.  Per
+ * producer->consumer buffer edge: intra vs inter.  Arrays are caller-owned,
+ * sized as documented; counts are returned. */
+typedef struct {
+  int32_t node, buf;
+  int32_t is_write;    /* 1: (b,k) in E_I (a write to the device); 0: (k,b) in E_O (a read back) */
+  int32_t isolated;    /* 1: isolated copy; 0: dependent copy */
+} dag_copy_class;
+
+typedef struct {
+  int32_t src_node, src_buf, dst_node, dst_buf;
+  int32_t inter;       /* 1: endpoints in different task components */
+} dag_edge_class;
+
+typedef struct {
+  int32_t n_nodes;
+  int32_t *cls;                /* [n_nodes] FRONT|END|IN bits */
+  int32_t *topo;               /* [n_nodes] Kahn order, smallest id first */
+  dag_copy_class *copies;      /* [cap_copies] */
+  int32_t cap_copies, n_copies;
+  dag_edge_class *edge_cls;    /* [cap_edges] */
+  int32_t cap_edges, n_edge_cls;
+} dag_analysis;
+
+dag_status dag_analyze(const dag_node_desc *nodes, int n_nodes, const dag_edge *edges, int n_edges,
+                       const dag_buffer_desc *buffers, int n_buffers, dag_analysis *out);
+
+/* One executed tile: output region of one kernel, with the tickets it drew
+ * from one global counter after acquiring its inputs (start) and after
+ * writing its output, before releasing it (end), %globaltimer times (ns) and
+ * the SM it ran on. */
+typedef struct {
+  int32_t node, r0, r1, c0, c1;   /* region of the kernel's output buffer */
+  uint32_t start_ticket, end_ticket;
+  uint32_t smid;
+  uint64_t t_start_ns, t_end_ns;
+} dag_trace_record;
+
+/* dag_trace_get: records of the last submit in queue order (needs
+ * opts.trace; call after dag_wait); *n = number of tiles. */
+dag_status dag_trace_get(dag_handle *h, dag_trace_record *out, int cap, int *n);
+
+/* Static plan facts. */
+typedef struct {
+  int32_t n_tiles, n_counters, n_waits, grid;
+  int32_t smem_bytes;
+  double flops, bytes;           /* algorithmic totals (2MNK per GEMM; each operand read once + output written once) */
+  double critical_path_us;       /* sum over the critical path of max(flops/peak, bytes/bw) under the peaks given to dag_set_peaks */
+  double work_bound_us;          /* max(critical path, total flops/peak, total bytes/bw) */
+} dag_plan_info;
+
+dag_status dag_plan_get(dag_handle *h, dag_plan_info *out);
+
+/* Per-tile static description in queue order: {node, r0, r1, c0, c1, cfg}. */
+dag_status dag_tiles_get(dag_handle *h, int32_t *out6, int cap, int *n);
+
+/* Host-only planning, no device needed: the tiles in queue order (as
+ * dag_tiles_get) that dag_create would build for a GPU with n_sm SMs running
+ * one executor CTA per SM.  info may be NULL. */
+dag_status dag_plan_host(const dag_node_desc *nodes, int n_nodes, const dag_edge *edges, int n_edges,
+                         const dag_buffer_desc *buffers, int n_buffers, const dag_options *opts, int n_sm,
+                         int32_t *out6, int cap, int *n_tiles, dag_plan_info *info);
+
+/* Peaks used by the roofline estimates and the time model (TFLOP/s, GB/s). */
+void dag_set_peaks(double bf16_tflops, double f32_tflops, double hbm_gbs);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DAGEXEC_H */

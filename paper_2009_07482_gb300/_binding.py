@@ -1,0 +1,252 @@
+"""ctypes binding of libdagexec (include/dagexec.h): same names, argument
+marshalling only.  Every computation runs in the library's CUDA kernels; there
+is no Python or CPU fallback: if the compiled library is missing, importing
+this module's functions raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libdagexec.so")
+
+i32, u32, u64, f32 = C.c_int32, C.c_uint32, C.c_uint64, C.c_float
+
+# dag_status
+DAG_OK, DAG_EINVAL, DAG_ECYCLE, DAG_ESHAPE, DAG_EDTYPE, DAG_EMULTIWRITER, DAG_ENOMEM, DAG_EBUSY, \
+    DAG_ETIMEOUT, DAG_EDEVICE, DAG_EUNSUPPORTED = range(11)
+STATUS_NAMES = {0: "DAG_OK", 1: "DAG_EINVAL", 2: "DAG_ECYCLE", 3: "DAG_ESHAPE", 4: "DAG_EDTYPE",
+                5: "DAG_EMULTIWRITER", 6: "DAG_ENOMEM", 7: "DAG_EBUSY", 8: "DAG_ETIMEOUT", 9: "DAG_EDEVICE",
+                10: "DAG_EUNSUPPORTED"}
+DAG_F32, DAG_BF16 = 0, 1
+DAG_OP_GEMM, DAG_OP_ADD, DAG_OP_SOFTMAX, DAG_OP_UNARY = 0, 1, 2, 3
+DAG_ACT_NONE, DAG_ACT_RELU, DAG_ACT_GELU = 0, 1, 2
+DAG_BUF_INPUT, DAG_BUF_OUTPUT, DAG_BUF_RESIDENT = 1, 2, 4
+DAG_SCHED_RANK_MODEL, DAG_SCHED_RANK_GIVEN, DAG_SCHED_FIFO = 0, 1, 2
+
+
+class dag_buffer_desc(C.Structure):
+    _fields_ = [("rows", i32), ("cols", i32), ("dtype", i32), ("flags", u32), ("view_of", i32),
+                ("col_offset", i32)]
+
+
+class dag_node_desc(C.Structure):
+    _fields_ = [("op", i32), ("a", i32), ("b", i32), ("bias", i32), ("out", i32), ("trans_b", i32),
+                ("act", i32), ("scale", f32), ("batch", i32), ("component", i32)]
+
+
+class dag_edge(C.Structure):
+    _fields_ = [("src_node", i32), ("src_buf", i32), ("dst_node", i32), ("dst_buf", i32)]
+
+
+class dag_options(C.Structure):
+    _fields_ = [("timeout_ns", u64), ("trace", i32), ("max_ctas", i32), ("scheduler", i32),
+                ("tile_override", i32), ("node_cost_us", C.POINTER(f32)), ("debug_never_ready", i32),
+                ("reserved", i32 * 7)]
+
+
+class dag_copy_class(C.Structure):
+    _fields_ = [("node", i32), ("buf", i32), ("is_write", i32), ("isolated", i32)]
+
+
+class dag_edge_class(C.Structure):
+    _fields_ = [("src_node", i32), ("src_buf", i32), ("dst_node", i32), ("dst_buf", i32), ("inter", i32)]
+
+
+class dag_analysis(C.Structure):
+    _fields_ = [("n_nodes", i32), ("cls", C.POINTER(i32)), ("topo", C.POINTER(i32)),
+                ("copies", C.POINTER(dag_copy_class)), ("cap_copies", i32), ("n_copies", i32),
+                ("edge_cls", C.POINTER(dag_edge_class)), ("cap_edges", i32), ("n_edge_cls", i32)]
+
+
+class dag_trace_record(C.Structure):
+    _fields_ = [("node", i32), ("r0", i32), ("r1", i32), ("c0", i32), ("c1", i32), ("start_ticket", u32),
+                ("end_ticket", u32), ("smid", u32), ("t_start_ns", u64), ("t_end_ns", u64)]
+
+
+class dag_plan_info(C.Structure):
+    _fields_ = [("n_tiles", i32), ("n_counters", i32), ("n_waits", i32), ("grid", i32), ("smem_bytes", i32),
+                ("flops", C.c_double), ("bytes", C.c_double), ("critical_path_us", C.c_double),
+                ("work_bound_us", C.c_double)]
+
+
+class DagError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+
+
+_lib = None
+_lock = threading.Lock()
+
+_SIGS = {
+    "dag_create": (i32, [C.POINTER(dag_node_desc), C.c_int, C.POINTER(dag_edge), C.c_int,
+                         C.POINTER(dag_buffer_desc), C.c_int, C.POINTER(dag_options), C.POINTER(C.c_void_p)]),
+    "dag_set_input": (i32, [C.c_void_p, C.c_int, C.c_void_p]),
+    "dag_set_output": (i32, [C.c_void_p, C.c_int, C.c_void_p]),
+    "dag_submit": (i32, [C.c_void_p, C.c_void_p]),
+    "dag_submit_coarse": (i32, [C.c_void_p, C.c_void_p]),
+    "dag_wait": (i32, [C.c_void_p, u64]),
+    "dag_get_output": (i32, [C.c_void_p, C.c_int, C.c_void_p]),
+    "dag_device_ptr": (C.c_void_p, [C.c_void_p, C.c_int, C.POINTER(C.c_int64)]),
+    "dag_destroy": (i32, [C.c_void_p]),
+    "dag_last_error": (C.c_char_p, []),
+    "dag_host_alloc": (C.c_void_p, [C.c_size_t]),
+    "dag_host_free": (None, [C.c_void_p]),
+    "dag_analyze": (i32, [C.POINTER(dag_node_desc), C.c_int, C.POINTER(dag_edge), C.c_int,
+                          C.POINTER(dag_buffer_desc), C.c_int, C.POINTER(dag_analysis)]),
+    "dag_trace_get": (i32, [C.c_void_p, C.POINTER(dag_trace_record), C.c_int, C.POINTER(C.c_int)]),
+    "dag_plan_get": (i32, [C.c_void_p, C.POINTER(dag_plan_info)]),
+    "dag_tiles_get": (i32, [C.c_void_p, C.POINTER(i32), C.c_int, C.POINTER(C.c_int)]),
+    "dag_plan_host": (i32, [C.POINTER(dag_node_desc), C.c_int, C.POINTER(dag_edge), C.c_int,
+                            C.POINTER(dag_buffer_desc), C.c_int, C.POINTER(dag_options), C.c_int,
+                            C.POINTER(i32), C.c_int, C.POINTER(C.c_int), C.POINTER(dag_plan_info)]),
+    "dag_set_peaks": (None, [C.c_double, C.c_double, C.c_double]),
+}
+
+
+def lib():
+    """The loaded library; raises if it has not been built (no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libdagexec.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+            L = C.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().dag_last_error().decode(errors="replace")
+
+
+def check(status: int, where: str) -> None:
+    if status != DAG_OK:
+        raise DagError(status, where, last_error())
+
+
+# thin wrappers with the C names ------------------------------------------------
+def _arr(ctype, items):
+    items = list(items)
+    return (ctype * max(1, len(items)))(*items), len(items)
+
+
+def dag_create(nodes, edges, buffers, options: Optional[dag_options] = None) -> C.c_void_p:
+    na, nn = _arr(dag_node_desc, nodes)
+    ea, ne = _arr(dag_edge, edges)
+    ba, nb = _arr(dag_buffer_desc, buffers)
+    h = C.c_void_p()
+    check(lib().dag_create(na, nn, ea, ne, ba, nb, C.byref(options) if options else None, C.byref(h)), "dag_create")
+    return h
+
+
+def dag_analyze(nodes, edges, buffers, cap: int = 4096) -> dict:
+    na, nn = _arr(dag_node_desc, nodes)
+    ea, ne = _arr(dag_edge, edges)
+    ba, nb = _arr(dag_buffer_desc, buffers)
+    cls = (i32 * max(1, nn))()
+    topo = (i32 * max(1, nn))()
+    copies = (dag_copy_class * cap)()
+    ecls = (dag_edge_class * cap)()
+    a = dag_analysis(nn, cls, topo, copies, cap, 0, ecls, cap, 0)
+    check(lib().dag_analyze(na, nn, ea, ne, ba, nb, C.byref(a)), "dag_analyze")
+    return {
+        "cls": list(cls[:nn]), "topo": list(topo[:nn]),
+        "copies": [(c.node, c.buf, c.is_write, c.isolated) for c in copies[:min(cap, a.n_copies)]],
+        "edges": [(e.src_node, e.src_buf, e.dst_node, e.dst_buf, e.inter) for e in ecls[:min(cap, a.n_edge_cls)]],
+    }
+
+
+def dag_plan_host(nodes, edges, buffers, options: Optional[dag_options] = None, n_sm: int = 148):
+    na, nn = _arr(dag_node_desc, nodes)
+    ea, ne = _arr(dag_edge, edges)
+    ba, nb = _arr(dag_buffer_desc, buffers)
+    n = C.c_int(0)
+    info = dag_plan_info()
+    opt = C.byref(options) if options else None
+    check(lib().dag_plan_host(na, nn, ea, ne, ba, nb, opt, n_sm, None, 0, C.byref(n), C.byref(info)), "dag_plan_host")
+    out = (i32 * (6 * max(1, n.value)))()
+    check(lib().dag_plan_host(na, nn, ea, ne, ba, nb, opt, n_sm, out, n.value, C.byref(n), None), "dag_plan_host")
+    import numpy as np
+    return np.frombuffer(out, dtype=np.int32)[: 6 * n.value].reshape(-1, 6).copy(), info
+
+
+def dag_set_input(h, buf: int, host_ptr) -> None:
+    check(lib().dag_set_input(h, buf, host_ptr), "dag_set_input")
+
+
+def dag_set_output(h, buf: int, host_ptr) -> None:
+    check(lib().dag_set_output(h, buf, host_ptr), "dag_set_output")
+
+
+def dag_submit(h, stream: int = 0) -> None:
+    check(lib().dag_submit(h, C.c_void_p(stream)), "dag_submit")
+
+
+def dag_submit_coarse(h, stream: int = 0) -> None:
+    check(lib().dag_submit_coarse(h, C.c_void_p(stream)), "dag_submit_coarse")
+
+
+def dag_wait(h, timeout_ns: int = 30_000_000_000) -> int:
+    """Returns the status (does not raise on DAG_ETIMEOUT so callers can test it)."""
+    return int(lib().dag_wait(h, timeout_ns))
+
+
+def dag_get_output(h, buf: int, host_ptr) -> None:
+    check(lib().dag_get_output(h, buf, host_ptr), "dag_get_output")
+
+
+def dag_device_ptr(h, buf: int):
+    ld = C.c_int64(0)
+    p = lib().dag_device_ptr(h, buf, C.byref(ld))
+    return p, ld.value
+
+
+def dag_destroy(h) -> None:
+    check(lib().dag_destroy(h), "dag_destroy")
+
+
+def dag_host_alloc(nbytes: int) -> int:
+    p = lib().dag_host_alloc(nbytes)
+    if not p:
+        raise DagError(DAG_ENOMEM, "dag_host_alloc", last_error())
+    return p
+
+
+def dag_host_free(p) -> None:
+    lib().dag_host_free(p)
+
+
+def dag_trace_get(h):
+    n = C.c_int(0)
+    check(lib().dag_trace_get(h, None, 0, C.byref(n)), "dag_trace_get")
+    recs = (dag_trace_record * max(1, n.value))()
+    check(lib().dag_trace_get(h, recs, n.value, C.byref(n)), "dag_trace_get")
+    return recs[: n.value]
+
+
+def dag_plan_get(h) -> dag_plan_info:
+    info = dag_plan_info()
+    check(lib().dag_plan_get(h, C.byref(info)), "dag_plan_get")
+    return info
+
+
+def dag_tiles_get(h):
+    import numpy as np
+    n = C.c_int(0)
+    check(lib().dag_tiles_get(h, None, 0, C.byref(n)), "dag_tiles_get")
+    out = (i32 * (6 * max(1, n.value)))()
+    check(lib().dag_tiles_get(h, out, n.value, C.byref(n)), "dag_tiles_get")
+    return np.frombuffer(out, dtype=np.int32)[: 6 * n.value].reshape(-1, 6).copy()
+
+
+def dag_set_peaks(bf16_tflops: float, f32_tflops: float, hbm_gbs: float) -> None:
+    lib().dag_set_peaks(bf16_tflops, f32_tflops, hbm_gbs)

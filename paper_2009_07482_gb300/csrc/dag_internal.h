@@ -1,0 +1,106 @@
+// dag_internal.h -- plan structures shared by the host planner and the
+// device executor of libdagexec (not part of the public ABI).
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dagx {
+
+// Tile kinds.  A tile is a rectangle of one kernel's output buffer.
+enum TileOp : int32_t {
+  T_GEMM_BF16 = 0,  // tcgen05 (TMEM accumulator), TMA-fed, 128 x BN
+  T_GEMM_F32 = 1,   // exact-f32 SIMT FFMA, BM x BN
+  T_ADD = 2,        // 128-bit elementwise add (+ activation)
+  T_UNARY = 3,      // 128-bit elementwise activation
+  T_SOFTMAX = 4     // warp-per-row softmax over whole rows
+};
+
+// f32 SIMT GEMM tile shapes (cfg field of a T_GEMM_F32 tile)
+enum F32Cfg : int32_t { F32_64x64 = 0, F32_128x64 = 1, F32_128x128 = 2 };
+
+constexpr int kThreads = 256;       // 8 warps per CTA
+constexpr int kBM = 128;            // bf16 GEMM tile rows (MMA M)
+constexpr int kBK = 64;             // bf16 K per stage (one 128-byte swizzle row)
+constexpr int kStages = 4;          // TMA -> MMA pipeline depth
+constexpr int kMaxBN = 256;
+constexpr int kStageA = kBM * kBK * 2;        // 16 KiB
+constexpr int kStageB = kMaxBN * kBK * 2;     // 32 KiB
+constexpr int kTmemCols = 256;                // one 128 x 256 f32 accumulator
+
+struct TileDesc {
+  int32_t node;   // kernel id
+  int32_t op;     // TileOp
+  int32_t r0, r1; // rows of the output buffer (row-stacked batches: within one batch)
+  int32_t c0, c1; // columns of the output buffer (view coordinates)
+  int32_t cfg;    // bf16: BN; f32: F32Cfg; others: 0
+  int32_t wait_begin, wait_count;  // into ExecParams::waits
+  int32_t rel_begin, rel_count;    // into ExecParams::rels
+  int32_t pad;
+};
+static_assert(sizeof(TileDesc) == 48, "TileDesc layout");
+
+// A dependency: counter[idx] must reach base(epoch) + target.  With
+// kWaitFlag set, idx is an input-buffer ready flag that must equal epoch+1.
+struct Wait {
+  uint32_t idx;
+  uint32_t target;
+};
+constexpr uint32_t kWaitFlag = 0x80000000u;
+
+struct NodeParams {
+  const void *A, *B, *bias;
+  void *C;
+  int64_t lda, ldb, ldc;   // row pitches in elements
+  int32_t M, N, K, batch;  // per-batch GEMM dims (M = rows for elementwise/softmax, N = cols)
+  int32_t trans_b, act;
+  float scale;
+  int32_t a_dt, b_dt, c_dt, bias_dt;  // 0 = f32, 1 = bf16
+  int32_t tmap_a, tmap_b;             // tensor-map indices (bf16 GEMM), else -1
+  int32_t vec;                        // 16-byte vector paths are aligned
+  int32_t pad;
+};
+
+struct Ctrl {
+  uint32_t head;        // next queue position (persistent mode)
+  uint32_t exit_count;  // CTAs that left the loop
+  uint32_t epoch;       // completed persistent launches
+  uint32_t ticket;      // trace ticket counter
+  uint32_t err_code;    // 0, or a DevErr
+  uint32_t err_tile;
+  uint32_t abort;       // set on error: every CTA leaves its waits
+  uint32_t pad;
+};
+
+enum DevErr : uint32_t { E_NONE = 0, E_DEP_TIMEOUT = 1, E_PIPE_TIMEOUT = 2, E_BAD_TILE = 3 };
+
+struct TraceRec {
+  uint32_t start_ticket, end_ticket, smid, tile;
+  uint64_t t_start, t_end;
+};
+
+struct ExecParams {
+  const TileDesc *tiles;
+  int32_t n_tiles;
+  int32_t mode;        // 0 = persistent queue, 1 = coarse (one tile per CTA, no waits)
+  int32_t tile_begin;  // coarse: first tile of this launch
+  int32_t trace_on;
+  const Wait *waits;
+  const uint32_t *rels;
+  const NodeParams *nodes;
+  const CUtensorMap *tmaps;
+  uint32_t *counters;
+  uint32_t *flags;
+  Ctrl *ctrl;
+  TraceRec *trace;
+  uint64_t timeout_ns;
+};
+
+// launchers (exec_kernel.cu)
+int exec_smem_bytes();
+cudaError_t exec_prepare();  // sets the kernel's shared-memory attribute (once per process)
+cudaError_t launch_persistent(const ExecParams &p, int grid, cudaStream_t s);
+cudaError_t launch_coarse(const ExecParams &p, int tile_begin, int n, cudaStream_t s);
+int max_coresident_ctas_per_sm();
+
+}  // namespace dagx

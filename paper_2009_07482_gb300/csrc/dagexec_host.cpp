@@ -1,0 +1,1169 @@
+// dagexec_host.cpp -- host planner and C ABI of libdagexec.
+//
+// dag_create turns the paper's application DAG (§3) into a device plan:
+//   1. validation: ids, shapes, dtypes, one writer per element, no in-place
+//      kernel, acyclic kernel graph (Kahn's algorithm, smallest id first);
+//   2. tiling: every kernel's output split into tiles (GEMM 128 x BN on the
+//      tensor cores for bf16, BM x BN SIMT for f32; softmax row blocks;
+//      elementwise row blocks);
+//   3. dependency counters: one u32 per (written buffer, row block); a tile
+//      increments the blocks it writes and waits until the blocks it reads
+//      reach their writer-tile count.  This is the paper's command-queue
+//      precedence E_Q (Def. 4 and rules i-iii after it) lifted from whole
+//      kernels to tiles;
+//   4. ordering: list scheduling of the tile graph on `grid` identical
+//      workers, ready tiles ranked by the bottom-level rank of their kernel
+//      (§5, clustering: the priority queue F ordered by bottom-level rank;
+//      HEFT's upward rank).  The result is a linear extension of the tile
+//      graph, which the persistent kernel's deadlock-freedom relies on;
+//   5. device memory, TMA tensor maps and the kernel parameter block.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <queue>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "dag_internal.h"
+#include "dagexec.h"
+
+using namespace dagx;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static dag_status fail(dag_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define CUDA_TRY(expr)                                                                         \
+  do {                                                                                         \
+    cudaError_t e_ = (expr);                                                                   \
+    if (e_ != cudaSuccess) return fail(DAG_EDEVICE, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+extern "C" const char *dag_last_error(void) { return g_err.c_str(); }
+
+// ---------------------------------------------------------------------------
+// peaks for the time model and the roofline estimates
+// ---------------------------------------------------------------------------
+static double g_bf16_tflops = 1918.4, g_f32_tflops = 60.0, g_hbm_gbs = 6695.2;
+
+extern "C" void dag_set_peaks(double bf16_tflops, double f32_tflops, double hbm_gbs) {
+  if (bf16_tflops > 0) g_bf16_tflops = bf16_tflops;
+  if (f32_tflops > 0) g_f32_tflops = f32_tflops;
+  if (hbm_gbs > 0) g_hbm_gbs = hbm_gbs;
+}
+
+// ---------------------------------------------------------------------------
+// driver entry points (no link-time dependency on libcuda)
+// ---------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 p_encode_tiled = nullptr;
+static PFN_cuStreamWriteValue32_v11070 p_write_value32 = nullptr;
+static std::once_flag g_driver_once;
+static std::string g_driver_err;
+
+static dag_status init_driver() {
+  std::call_once(g_driver_once, [] {
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void **)&p_encode_tiled, 12000,
+                                         cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p_encode_tiled)
+      g_driver_err = "cuTensorMapEncodeTiled not available";
+    if (cudaGetDriverEntryPointByVersion("cuStreamWriteValue32", (void **)&p_write_value32, 11070,
+                                         cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p_write_value32)
+      g_driver_err = "cuStreamWriteValue32 not available";
+    if (g_driver_err.empty() && exec_prepare() != cudaSuccess) g_driver_err = "cudaFuncSetAttribute failed";
+  });
+  if (!g_driver_err.empty()) return fail(DAG_EDEVICE, "%s", g_driver_err.c_str());
+  return DAG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// graph model
+// ---------------------------------------------------------------------------
+static inline int esize(int dt) { return dt == DAG_BF16 ? 2 : 4; }
+
+struct Region {  // rows [r0,r1) x cols [c0,c1) of a root buffer
+  int root, r0, r1, c0, c1;
+};
+static inline bool overlaps(const Region &a, const Region &b) {
+  return a.root == b.root && a.r0 < b.r1 && b.r0 < a.r1 && a.c0 < b.c1 && b.c0 < a.c1;
+}
+
+struct Graph {
+  int nb = 0, nn = 0;
+  std::vector<dag_buffer_desc> bufs;
+  std::vector<dag_node_desc> nodes;
+  std::vector<int> root, coff;           // per buffer
+  std::vector<std::vector<int>> succ, pred;
+  std::vector<int> topo, topo_pos;
+  std::vector<int> M, N, K;              // per node: per-batch GEMM dims, or rows/cols
+
+  Region full(int b) const {
+    return Region{root[b], 0, bufs[b].rows, coff[b], coff[b] + bufs[b].cols};
+  }
+  int inputs(int v, int out[3]) const {
+    int k = 0;
+    const dag_node_desc &n = nodes[v];
+    out[k++] = n.a;
+    if (n.op == DAG_OP_GEMM || n.op == DAG_OP_ADD) out[k++] = n.b;
+    if (n.op == DAG_OP_GEMM && n.bias >= 0) out[k++] = n.bias;
+    return k;
+  }
+};
+
+static dag_status build_graph(const dag_node_desc *nodes, int n_nodes, const dag_edge *edges, int n_edges,
+                              const dag_buffer_desc *buffers, int n_buffers, Graph &g) {
+  if (n_nodes < 0 || n_buffers < 0 || n_edges < 0) return fail(DAG_EINVAL, "negative count");
+  if ((n_nodes && !nodes) || (n_buffers && !buffers) || (n_edges && !edges))
+    return fail(DAG_EINVAL, "null array with a nonzero count");
+  g.nb = n_buffers;
+  g.nn = n_nodes;
+  g.bufs.assign(buffers, buffers + n_buffers);
+  g.nodes.assign(nodes, nodes + n_nodes);
+  g.root.resize(n_buffers);
+  g.coff.resize(n_buffers);
+  auto valid = [&](int id) { return id >= 0 && id < n_buffers; };
+  for (int i = 0; i < n_buffers; ++i) {
+    const dag_buffer_desc &b = buffers[i];
+    if (b.rows <= 0 || b.cols <= 0) return fail(DAG_ESHAPE, "buffer %d: shape %dx%d", i, b.rows, b.cols);
+    if (b.dtype != DAG_F32 && b.dtype != DAG_BF16) return fail(DAG_EDTYPE, "buffer %d: dtype %d", i, b.dtype);
+    if (b.flags & ~7u) return fail(DAG_EINVAL, "buffer %d: unknown flags", i);
+    if ((b.flags & DAG_BUF_RESIDENT) && !(b.flags & DAG_BUF_INPUT))
+      return fail(DAG_EINVAL, "buffer %d: RESIDENT without INPUT", i);
+    g.root[i] = i;
+    g.coff[i] = 0;
+    if (b.view_of >= 0) {
+      if (!valid(b.view_of) || b.view_of == i) return fail(DAG_EINVAL, "buffer %d: bad view parent", i);
+      const dag_buffer_desc &p = buffers[b.view_of];
+      if (p.view_of >= 0) return fail(DAG_EINVAL, "buffer %d: view of a view", i);
+      if (p.rows != b.rows || b.col_offset < 0 || b.col_offset + b.cols > p.cols)
+        return fail(DAG_ESHAPE, "buffer %d: view does not fit its parent", i);
+      if (p.dtype != b.dtype) return fail(DAG_EDTYPE, "buffer %d: view dtype differs from parent", i);
+      if (b.flags) return fail(DAG_EINVAL, "buffer %d: a view cannot carry INPUT/OUTPUT flags", i);
+      g.root[i] = b.view_of;
+      g.coff[i] = b.col_offset;
+    }
+  }
+  g.M.assign(n_nodes, 0);
+  g.N.assign(n_nodes, 0);
+  g.K.assign(n_nodes, 0);
+  for (int v = 0; v < n_nodes; ++v) {
+    const dag_node_desc &n = nodes[v];
+    if (!valid(n.a) || !valid(n.out)) return fail(DAG_EINVAL, "node %d: bad buffer id", v);
+    if (n.act < DAG_ACT_NONE || n.act > DAG_ACT_GELU) return fail(DAG_EINVAL, "node %d: bad activation", v);
+    const dag_buffer_desc &A = buffers[n.a], &O = buffers[n.out];
+    if (g.bufs[g.root[n.out]].flags & DAG_BUF_INPUT)
+      return fail(DAG_EMULTIWRITER, "node %d writes input buffer %d", v, n.out);
+    switch (n.op) {
+      case DAG_OP_GEMM: {
+        if (!valid(n.b)) return fail(DAG_EINVAL, "node %d: bad B id", v);
+        if (n.batch < 1) return fail(DAG_EINVAL, "node %d: batch %d", v, n.batch);
+        const dag_buffer_desc &B = buffers[n.b];
+        if (A.rows % n.batch || B.rows % n.batch) return fail(DAG_ESHAPE, "node %d: batch does not divide rows", v);
+        const int M = A.rows / n.batch, K = A.cols;
+        const int N = n.trans_b ? B.rows / n.batch : B.cols;
+        const int Kb = n.trans_b ? B.cols : B.rows / n.batch;
+        if (Kb != K) return fail(DAG_ESHAPE, "node %d: inner dims %d vs %d", v, K, Kb);
+        if (O.rows != A.rows || O.cols != N) return fail(DAG_ESHAPE, "node %d: output %dx%d, want %dx%d", v, O.rows, O.cols, A.rows, N);
+        if (A.dtype != B.dtype) return fail(DAG_EDTYPE, "node %d: A and B dtypes differ", v);
+        if (n.bias >= 0) {
+          if (!valid(n.bias)) return fail(DAG_EINVAL, "node %d: bad bias id", v);
+          if (buffers[n.bias].rows != 1 || buffers[n.bias].cols != N) return fail(DAG_ESHAPE, "node %d: bias shape", v);
+        }
+        g.M[v] = M; g.N[v] = N; g.K[v] = K;
+        break;
+      }
+      case DAG_OP_ADD:
+        if (!valid(n.b)) return fail(DAG_EINVAL, "node %d: bad B id", v);
+        if (buffers[n.b].rows != O.rows || buffers[n.b].cols != O.cols || A.rows != O.rows || A.cols != O.cols)
+          return fail(DAG_ESHAPE, "node %d: add shapes", v);
+        g.M[v] = O.rows; g.N[v] = O.cols; g.K[v] = 0;
+        break;
+      case DAG_OP_SOFTMAX:
+      case DAG_OP_UNARY:
+        if (A.rows != O.rows || A.cols != O.cols) return fail(DAG_ESHAPE, "node %d: shapes", v);
+        g.M[v] = O.rows; g.N[v] = O.cols; g.K[v] = 0;
+        break;
+      default:
+        return fail(DAG_EINVAL, "node %d: unknown op %d", v, n.op);
+    }
+  }
+  // one writer per element, no in-place kernel
+  for (int u = 0; u < n_nodes; ++u) {
+    const Region wu = g.full(nodes[u].out);
+    for (int v = u + 1; v < n_nodes; ++v)
+      if (overlaps(wu, g.full(nodes[v].out)))
+        return fail(DAG_EMULTIWRITER, "nodes %d and %d write overlapping buffers", u, v);
+    int in[3];
+    const int k = g.inputs(u, in);
+    for (int q = 0; q < k; ++q)
+      if (overlaps(wu, g.full(in[q]))) return fail(DAG_EMULTIWRITER, "node %d reads what it writes", u);
+  }
+  // kernel graph: u -> v when v reads a region u writes
+  g.succ.assign(n_nodes, {});
+  g.pred.assign(n_nodes, {});
+  for (int v = 0; v < n_nodes; ++v) {
+    int in[3];
+    const int k = g.inputs(v, in);
+    for (int u = 0; u < n_nodes; ++u) {
+      if (u == v) continue;
+      const Region w = g.full(nodes[u].out);
+      for (int q = 0; q < k; ++q)
+        if (overlaps(w, g.full(in[q]))) {
+          g.succ[u].push_back(v);
+          g.pred[v].push_back(u);
+          break;
+        }
+    }
+    // every element read must be written by some kernel or be an input
+    for (int q = 0; q < k; ++q) {
+      const Region r = g.full(in[q]);
+      if (g.bufs[r.root].flags & DAG_BUF_INPUT) continue;
+      std::vector<std::pair<int, int>> cov;
+      for (int u = 0; u < n_nodes; ++u) {
+        const Region w = g.full(nodes[u].out);
+        if (w.root == r.root) cov.push_back({w.c0, w.c1});
+      }
+      std::sort(cov.begin(), cov.end());
+      int reach = r.c0;
+      for (auto &c : cov)
+        if (c.first <= reach) reach = std::max(reach, c.second);
+      if (reach < r.c1) return fail(DAG_EINVAL, "node %d reads buffer %d, which is neither an input nor fully written", v, in[q]);
+    }
+  }
+  // edges given by the caller must be implied by the buffers
+  for (int e = 0; e < n_edges; ++e) {
+    const dag_edge &E = edges[e];
+    if (E.src_node < 0 || E.src_node >= n_nodes || E.dst_node < 0 || E.dst_node >= n_nodes || !valid(E.src_buf) ||
+        !valid(E.dst_buf))
+      return fail(DAG_EINVAL, "edge %d: bad id", e);
+    if (nodes[E.src_node].out != E.src_buf) return fail(DAG_EINVAL, "edge %d: node %d does not write buffer %d", e, E.src_node, E.src_buf);
+    int in[3];
+    const int k = g.inputs(E.dst_node, in);
+    bool reads = false;
+    for (int q = 0; q < k; ++q) reads |= in[q] == E.dst_buf;
+    if (!reads) return fail(DAG_EINVAL, "edge %d: node %d does not read buffer %d", e, E.dst_node, E.dst_buf);
+    if (!overlaps(g.full(E.src_buf), g.full(E.dst_buf))) return fail(DAG_EINVAL, "edge %d: buffers do not overlap", e);
+  }
+  // Kahn, smallest id first
+  std::vector<int> indeg(n_nodes, 0);
+  for (int v = 0; v < n_nodes; ++v) indeg[v] = (int)g.pred[v].size();
+  std::priority_queue<int, std::vector<int>, std::greater<int>> ready;
+  for (int v = 0; v < n_nodes; ++v)
+    if (!indeg[v]) ready.push(v);
+  g.topo.clear();
+  while (!ready.empty()) {
+    const int u = ready.top();
+    ready.pop();
+    g.topo.push_back(u);
+    for (int v : g.succ[u])
+      if (--indeg[v] == 0) ready.push(v);
+  }
+  if ((int)g.topo.size() != n_nodes) return fail(DAG_ECYCLE, "the kernel graph has a cycle");
+  g.topo_pos.assign(n_nodes, 0);
+  for (int i = 0; i < n_nodes; ++i) g.topo_pos[g.topo[i]] = i;
+  return DAG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// dag_analyze: §3 Defs. 1-3 and the copy / edge classification
+// ---------------------------------------------------------------------------
+extern "C" dag_status dag_analyze(const dag_node_desc *nodes, int n_nodes, const dag_edge *edges, int n_edges,
+                                  const dag_buffer_desc *buffers, int n_buffers, dag_analysis *out) {
+  if (!out) return fail(DAG_EINVAL, "null output");
+  Graph g;
+  dag_status s = build_graph(nodes, n_nodes, edges, n_edges, buffers, n_buffers, g);
+  if (s) return s;
+  out->n_nodes = n_nodes;
+  out->n_copies = 0;
+  out->n_edge_cls = 0;
+  for (int v = 0; v < n_nodes; ++v) {
+    // FRONT(T): no input produced inside T (every producer, if any, lies in another component)
+    // END(T):   no output consumed inside T
+    bool front = true, end = true;
+    for (int u : g.pred[v])
+      if (nodes[u].component == nodes[v].component) front = false;
+    for (int w : g.succ[v])
+      if (nodes[w].component == nodes[v].component) end = false;
+    int c = (front ? 1 : 0) | (end ? 2 : 0);
+    if (!front && !end) c |= 4;  // IN(T)
+    if (out->cls) out->cls[v] = c;
+    if (out->topo) out->topo[v] = g.topo[v];
+  }
+  auto add_copy = [&](int node, int buf, int is_write, int isolated) {
+    if (out->copies && out->n_copies < out->cap_copies)
+      out->copies[out->n_copies] = dag_copy_class{node, buf, is_write, isolated};
+    out->n_copies++;
+  };
+  for (int v = 0; v < n_nodes; ++v) {
+    int in[3];
+    const int k = g.inputs(v, in);
+    for (int q = 0; q < k; ++q) {
+      bool produced = false;
+      for (int u : g.pred[v]) produced |= overlaps(g.full(nodes[u].out), g.full(in[q]));
+      add_copy(v, in[q], 1, produced ? 0 : 1);  // (b,k) in E_I: isolated write iff no (b',b) in E
+    }
+    bool consumed = !g.succ[v].empty();
+    add_copy(v, nodes[v].out, 0, consumed ? 0 : 1);  // (k,b) in E_O: isolated read iff no (b,b') in E
+  }
+  for (int u = 0; u < n_nodes; ++u)
+    for (int v : g.succ[u]) {
+      int in[3];
+      const int k = g.inputs(v, in);
+      for (int q = 0; q < k; ++q) {
+        if (!overlaps(g.full(nodes[u].out), g.full(in[q]))) continue;
+        if (out->edge_cls && out->n_edge_cls < out->cap_edges)
+          out->edge_cls[out->n_edge_cls] =
+              dag_edge_class{u, nodes[u].out, v, in[q], nodes[u].component != nodes[v].component ? 1 : 0};
+        out->n_edge_cls++;
+      }
+    }
+  return DAG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// plan
+// ---------------------------------------------------------------------------
+struct Plan {
+  Graph g;
+  dag_options opt{};
+  int n_sm = 148, grid = 148;
+  std::vector<int> cfg;                 // per node tile config
+  std::vector<TileDesc> tiles;          // node-major creation order
+  std::vector<int> node_first, node_count;
+  std::vector<TileDesc> queue;          // queue order (persistent mode)
+  std::vector<int> queue_src;           // queue position -> creation index
+  std::vector<Wait> waits;
+  std::vector<uint32_t> rels;
+  int n_counters = 0;
+  std::vector<int> flag_of_root;        // streamed-input flag index, or -1
+  int n_flags = 0;
+  std::vector<double> rank;             // per node bottom-level rank (us)
+  std::vector<double> node_cost;        // per node estimated time (us)
+  double flops = 0, bytes = 0, cp_us = 0, work_us = 0;
+};
+
+static int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// per-tile time model (us): roofline of the tile's work on one SM plus a
+// fixed per-tile overhead
+static double tile_time_us(const Plan &P, int v, const TileDesc &t) {
+  const Graph &g = P.g;
+  const dag_node_desc &n = g.nodes[v];
+  const double per_sm_bw = g_hbm_gbs * 1e9 / P.n_sm * 2.0;  // an SM alone streams faster than its fair share
+  const double rows = t.r1 - t.r0, cols = t.c1 - t.c0;
+  if (n.op == DAG_OP_GEMM) {
+    const double K = g.K[v];
+    const double flops = 2.0 * rows * cols * K;
+    const int ea = esize(g.bufs[n.a].dtype);
+    const double bytes = (rows + cols) * K * ea + rows * cols * esize(g.bufs[n.out].dtype);
+    double rate;
+    if (t.op == T_GEMM_BF16) {
+      const double eff = t.cfg >= 256 ? 0.8 : t.cfg >= 128 ? 0.7 : 0.5;
+      rate = g_bf16_tflops * 1e12 / P.n_sm * eff;
+    } else {
+      rate = g_f32_tflops * 1e12 / P.n_sm * 0.6;
+    }
+    return std::max(flops / rate, bytes / per_sm_bw) * 1e6 + 1.0;
+  }
+  double bytes = rows * cols * (esize(g.bufs[n.a].dtype) + esize(g.bufs[n.out].dtype));
+  if (n.op == DAG_OP_ADD) bytes += rows * cols * esize(g.bufs[n.b].dtype);
+  return bytes / per_sm_bw * 1e6 + 0.7;
+}
+
+static int ntiles_gemm(const Graph &g, int v, int bm, int bn) {
+  return g.nodes[v].batch * ((g.M[v] + bm - 1) / bm) * ((g.N[v] + bn - 1) / bn);
+}
+
+// tile shapes: bf16 GEMMs take the widest BN (256/128/64) that still gives
+// the kernel's concurrency level enough tiles to fill the GPU; f32 GEMMs
+// likewise among 128x128 / 128x64 / 64x64.
+static void choose_configs(Plan &P) {
+  Graph &g = P.g;
+  const int nn = g.nn;
+  std::vector<int> depth(nn, 0);
+  for (int u : g.topo)
+    for (int v : g.succ[u]) depth[v] = std::max(depth[v], depth[u] + 1);
+  int maxd = 0;
+  for (int v = 0; v < nn; ++v) maxd = std::max(maxd, depth[v]);
+  P.cfg.assign(nn, 0);
+  static const int bns[3] = {256, 128, 64};
+  static const int f32c[3][3] = {{F32_128x128, 128, 128}, {F32_128x64, 128, 64}, {F32_64x64, 64, 64}};
+  for (int pass = 0; pass < 3; ++pass) {
+    // concurrency of a depth level at option index `pass`
+    std::vector<long> level(maxd + 1, 0);
+    for (int v = 0; v < nn; ++v) {
+      const dag_node_desc &n = g.nodes[v];
+      if (n.op != DAG_OP_GEMM) { level[depth[v]] += 8; continue; }
+      if (g.bufs[n.a].dtype == DAG_BF16) level[depth[v]] += ntiles_gemm(g, v, 128, bns[pass]);
+      else level[depth[v]] += ntiles_gemm(g, v, f32c[pass][1], f32c[pass][2]);
+    }
+    for (int v = 0; v < nn; ++v) {
+      const dag_node_desc &n = g.nodes[v];
+      if (n.op != DAG_OP_GEMM || P.cfg[v]) continue;
+      const bool enough = level[depth[v]] >= P.n_sm * 3 / 4 || pass == 2;
+      if (!enough) continue;
+      if (g.bufs[n.a].dtype == DAG_BF16) {
+        int bn = bns[pass];
+        while (bn > 64 && bn / 2 >= round_up(g.N[v], 64)) bn /= 2;  // no wider than N
+        P.cfg[v] = bn;
+      } else {
+        P.cfg[v] = f32c[pass][0] + 100;  // +100 marks "set"
+      }
+    }
+  }
+  for (int v = 0; v < nn; ++v) {
+    const dag_node_desc &n = g.nodes[v];
+    if (n.op != DAG_OP_GEMM) continue;
+    if (g.bufs[n.a].dtype == DAG_BF16) {
+      if (P.opt.tile_override == 64 || P.opt.tile_override == 128 || P.opt.tile_override == 256)
+        P.cfg[v] = P.opt.tile_override;
+    } else {
+      P.cfg[v] -= 100;
+    }
+  }
+}
+
+static void make_tiles(Plan &P) {
+  Graph &g = P.g;
+  P.tiles.clear();
+  P.node_first.assign(g.nn, 0);
+  P.node_count.assign(g.nn, 0);
+  for (int v = 0; v < g.nn; ++v) {
+    const dag_node_desc &n = g.nodes[v];
+    P.node_first[v] = (int)P.tiles.size();
+    auto push = [&](int op, int r0, int r1, int c0, int c1, int cfg) {
+      TileDesc t{};
+      t.node = v; t.op = op; t.r0 = r0; t.r1 = r1; t.c0 = c0; t.c1 = c1; t.cfg = cfg;
+      P.tiles.push_back(t);
+    };
+    const int R = g.bufs[n.out].rows, C = g.bufs[n.out].cols;
+    if (n.op == DAG_OP_GEMM) {
+      const bool bf = g.bufs[n.a].dtype == DAG_BF16;
+      int bm, bn;
+      if (bf) { bm = kBM; bn = P.cfg[v]; }
+      else {
+        bm = P.cfg[v] == F32_64x64 ? 64 : 128;
+        bn = P.cfg[v] == F32_128x128 ? 128 : 64;
+      }
+      const int M = g.M[v], N = g.N[v];
+      for (int b = 0; b < n.batch; ++b)
+        for (int m = 0; m < M; m += bm)
+          for (int c = 0; c < N; c += bn)
+            push(bf ? T_GEMM_BF16 : T_GEMM_F32, b * M + m, b * M + std::min(m + bm, M), c, std::min(c + bn, N), P.cfg[v]);
+    } else if (n.op == DAG_OP_SOFTMAX) {
+      const int rows = C <= 1024 ? 128 : 32;
+      for (int r = 0; r < R; r += rows) push(T_SOFTMAX, r, std::min(r + rows, R), 0, C, 0);
+    } else {
+      int rows = 256;
+      while (rows > 8 && (long)rows * C > 131072) rows /= 2;
+      for (int r = 0; r < R; r += rows)
+        push(n.op == DAG_OP_ADD ? T_ADD : T_UNARY, r, std::min(r + rows, R), 0, C, 0);
+    }
+    P.node_count[v] = (int)P.tiles.size() - P.node_first[v];
+  }
+}
+
+// row ranges a tile reads, per input buffer (rows of that buffer)
+static int tile_reads(const Graph &g, const TileDesc &t, int buf[3], int r0[3], int r1[3]) {
+  const dag_node_desc &n = g.nodes[t.node];
+  int k = 0;
+  if (n.op == DAG_OP_GEMM) {
+    const int M = g.M[t.node], N = g.N[t.node], K = g.K[t.node];
+    const int bt = t.r0 / M;
+    buf[k] = n.a; r0[k] = t.r0; r1[k] = t.r1; ++k;
+    buf[k] = n.b;
+    if (n.trans_b) { r0[k] = bt * N + t.c0; r1[k] = bt * N + t.c1; }
+    else { r0[k] = bt * K; r1[k] = bt * K + K; }
+    ++k;
+    if (n.bias >= 0) { buf[k] = n.bias; r0[k] = 0; r1[k] = 1; ++k; }
+  } else {
+    buf[k] = n.a; r0[k] = t.r0; r1[k] = t.r1; ++k;
+    if (n.op == DAG_OP_ADD) { buf[k] = n.b; r0[k] = t.r0; r1[k] = t.r1; ++k; }
+  }
+  return k;
+}
+
+// counters, waits, releases and the tile graph derived from them
+static void build_deps(Plan &P, std::vector<std::vector<int>> &tile_pred) {
+  Graph &g = P.g;
+  const int nt = (int)P.tiles.size();
+  // row granularity per written root
+  std::vector<int> gran(g.nb, 0), base(g.nb, -1), nblk(g.nb, 0);
+  for (int i = 0; i < nt; ++i) {
+    const TileDesc &t = P.tiles[i];
+    const int root = g.root[g.nodes[t.node].out];
+    const int rows = g.bufs[root].rows;
+    int gg = gran[root] ? gran[root] : 128;
+    while (gg > 16 && ((t.r0 % gg) || ((t.r1 % gg) && t.r1 != rows))) gg /= 2;
+    gran[root] = gg;
+  }
+  int nc = 0;
+  for (int r = 0; r < g.nb; ++r)
+    if (gran[r]) {
+      base[r] = nc;
+      nblk[r] = (g.bufs[r].rows + gran[r] - 1) / gran[r];
+      nc += nblk[r];
+    }
+  std::vector<uint32_t> target(nc, 0);
+  std::vector<std::vector<int>> incr(nc);
+  std::vector<std::vector<uint32_t>> rel_of(nt);
+  for (int i = 0; i < nt; ++i) {
+    const TileDesc &t = P.tiles[i];
+    const int root = g.root[g.nodes[t.node].out];
+    for (int b = t.r0 / gran[root]; b <= (t.r1 - 1) / gran[root]; ++b) {
+      const int c = base[root] + b;
+      target[c]++;
+      incr[c].push_back(i);
+      rel_of[i].push_back((uint32_t)c);
+    }
+  }
+  // streamed input flags
+  P.flag_of_root.assign(g.nb, -1);
+  P.n_flags = 0;
+  for (int r = 0; r < g.nb; ++r)
+    if (g.bufs[r].view_of < 0 && (g.bufs[r].flags & DAG_BUF_INPUT) && !(g.bufs[r].flags & DAG_BUF_RESIDENT))
+      P.flag_of_root[r] = P.n_flags++;
+  if (P.opt.debug_never_ready > 0) nc += 1;  // a counter nothing releases
+  P.n_counters = nc;
+
+  std::vector<std::vector<Wait>> waits_of(nt);
+  tile_pred.assign(nt, {});
+  for (int i = 0; i < nt; ++i) {
+    const TileDesc &t = P.tiles[i];
+    int buf[3], r0[3], r1[3];
+    const int k = tile_reads(g, t, buf, r0, r1);
+    std::vector<Wait> &W = waits_of[i];
+    for (int q = 0; q < k; ++q) {
+      const int root = g.root[buf[q]];
+      if (P.flag_of_root[root] >= 0) {
+        W.push_back(Wait{kWaitFlag | (uint32_t)P.flag_of_root[root], 1u});
+        continue;
+      }
+      if (!gran[root]) continue;  // resident input
+      for (int b = r0[q] / gran[root]; b <= (r1[q] - 1) / gran[root]; ++b) {
+        const int c = base[root] + b;
+        W.push_back(Wait{(uint32_t)c, target[c]});
+        for (int u : incr[c]) tile_pred[i].push_back(u);
+      }
+    }
+    std::sort(W.begin(), W.end(), [](const Wait &a, const Wait &b) { return a.idx < b.idx; });
+    W.erase(std::unique(W.begin(), W.end(), [](const Wait &a, const Wait &b) { return a.idx == b.idx; }), W.end());
+    std::sort(tile_pred[i].begin(), tile_pred[i].end());
+    tile_pred[i].erase(std::unique(tile_pred[i].begin(), tile_pred[i].end()), tile_pred[i].end());
+  }
+  if (P.opt.debug_never_ready > 0) {
+    // the last `debug_never_ready` tiles in creation order wait on a counter no tile releases
+    for (int i = std::max(0, nt - P.opt.debug_never_ready); i < nt; ++i)
+      waits_of[i].push_back(Wait{(uint32_t)(nc - 1), 1u});
+  }
+  P.waits.clear();
+  P.rels.clear();
+  for (int i = 0; i < nt; ++i) {
+    TileDesc &t = P.tiles[i];
+    t.wait_begin = (int)P.waits.size();
+    t.wait_count = (int)waits_of[i].size();
+    P.waits.insert(P.waits.end(), waits_of[i].begin(), waits_of[i].end());
+    t.rel_begin = (int)P.rels.size();
+    t.rel_count = (int)rel_of[i].size();
+    P.rels.insert(P.rels.end(), rel_of[i].begin(), rel_of[i].end());
+  }
+}
+
+// bottom-level ranks and list-scheduled queue order
+static void order_tiles(Plan &P, const std::vector<std::vector<int>> &tile_pred) {
+  Graph &g = P.g;
+  const int nt = (int)P.tiles.size();
+  std::vector<double> est(nt);
+  for (int i = 0; i < nt; ++i) est[i] = tile_time_us(P, P.tiles[i].node, P.tiles[i]);
+  P.node_cost.assign(g.nn, 0.0);
+  for (int v = 0; v < g.nn; ++v) {
+    if (P.opt.scheduler == DAG_SCHED_RANK_GIVEN && P.opt.node_cost_us) {
+      P.node_cost[v] = P.opt.node_cost_us[v];
+      continue;
+    }
+    double t = 0;
+    for (int i = P.node_first[v]; i < P.node_first[v] + P.node_count[v]; ++i) t = std::max(t, est[i]);
+    const int waves = (P.node_count[v] + P.grid - 1) / P.grid;
+    P.node_cost[v] = t * waves;
+  }
+  P.rank.assign(g.nn, 0.0);
+  for (int i = g.nn - 1; i >= 0; --i) {
+    const int v = g.topo[i];
+    double m = 0;
+    for (int w : g.succ[v]) m = std::max(m, P.rank[w]);
+    P.rank[v] = P.node_cost[v] + m;
+  }
+  const bool fifo = P.opt.scheduler == DAG_SCHED_FIFO;
+
+  std::vector<std::vector<int>> tile_succ(nt);
+  std::vector<int> indeg(nt, 0);
+  for (int i = 0; i < nt; ++i) {
+    indeg[i] = (int)tile_pred[i].size();
+    for (int u : tile_pred[i]) tile_succ[u].push_back(i);
+  }
+  std::vector<double> ready_t(nt, 0.0);
+  // available set ordered by (rank desc, kernel topo position, creation index)
+  auto better = [&](int a, int b) {
+    const int va = P.tiles[a].node, vb = P.tiles[b].node;
+    if (!fifo && P.rank[va] != P.rank[vb]) return P.rank[va] < P.rank[vb];
+    if (g.topo_pos[va] != g.topo_pos[vb]) return g.topo_pos[va] > g.topo_pos[vb];
+    return a > b;
+  };
+  std::priority_queue<int, std::vector<int>, decltype(better)> avail(better);
+  using PI = std::pair<double, int>;
+  std::priority_queue<PI, std::vector<PI>, std::greater<PI>> pending;  // by ready time
+  std::priority_queue<double, std::vector<double>, std::greater<double>> workers;
+  for (int w = 0; w < P.grid; ++w) workers.push(0.0);
+  for (int i = 0; i < nt; ++i)
+    if (!indeg[i]) pending.push({0.0, i});
+  P.queue.clear();
+  P.queue_src.clear();
+  while (!pending.empty() || !avail.empty()) {
+    double now = workers.top();
+    if (avail.empty() && pending.top().first > now) now = pending.top().first;
+    while (!pending.empty() && pending.top().first <= now) {
+      avail.push(pending.top().second);
+      pending.pop();
+    }
+    const int t = avail.top();
+    avail.pop();
+    const double start = std::max(now, workers.top());
+    workers.pop();
+    const double fin = start + est[t];
+    workers.push(fin);
+    P.queue_src.push_back(t);
+    for (int s : tile_succ[t]) {
+      ready_t[s] = std::max(ready_t[s], fin);
+      if (--indeg[s] == 0) pending.push({ready_t[s], s});
+    }
+  }
+  P.queue.resize(nt);
+  for (int q = 0; q < nt; ++q) P.queue[q] = P.tiles[P.queue_src[q]];
+}
+
+// algorithmic totals and the critical-path roofline
+static void roofline(Plan &P) {
+  Graph &g = P.g;
+  std::vector<double> cost(g.nn, 0.0);
+  P.flops = P.bytes = 0;
+  for (int v = 0; v < g.nn; ++v) {
+    const dag_node_desc &n = g.nodes[v];
+    double f = 0, b = 0;
+    int in[3];
+    const int k = g.inputs(v, in);
+    for (int q = 0; q < k; ++q) b += (double)g.bufs[in[q]].rows * g.bufs[in[q]].cols * esize(g.bufs[in[q]].dtype);
+    b += (double)g.bufs[n.out].rows * g.bufs[n.out].cols * esize(g.bufs[n.out].dtype);
+    double peak;
+    if (n.op == DAG_OP_GEMM) {
+      f = 2.0 * n.batch * (double)g.M[v] * g.N[v] * g.K[v];
+      peak = (g.bufs[n.a].dtype == DAG_BF16 ? g_bf16_tflops : g_f32_tflops) * 1e12;
+    } else {
+      f = (double)g.bufs[n.out].rows * g.bufs[n.out].cols;
+      peak = 1e30;  // elementwise work is memory-bound
+    }
+    P.flops += n.op == DAG_OP_GEMM ? f : 0.0;
+    P.bytes += b;
+    cost[v] = std::max(n.op == DAG_OP_GEMM ? f / peak : 0.0, b / (g_hbm_gbs * 1e9)) * 1e6;
+  }
+  std::vector<double> fin(g.nn, 0.0);
+  double cp = 0;
+  for (int v : g.topo) {
+    double s = 0;
+    for (int u : g.pred[v]) s = std::max(s, fin[u]);
+    fin[v] = s + cost[v];
+    cp = std::max(cp, fin[v]);
+  }
+  P.cp_us = cp;
+  double f_bf = 0, f_32 = 0;
+  for (int v = 0; v < g.nn; ++v)
+    if (g.nodes[v].op == DAG_OP_GEMM) {
+      const double f = 2.0 * g.nodes[v].batch * (double)g.M[v] * g.N[v] * g.K[v];
+      (g.bufs[g.nodes[v].a].dtype == DAG_BF16 ? f_bf : f_32) += f;
+    }
+  const double work = (f_bf / (g_bf16_tflops * 1e12) + f_32 / (g_f32_tflops * 1e12)) * 1e6;
+  P.work_us = std::max(cp, std::max(work, P.bytes / (g_hbm_gbs * 1e9) * 1e6));
+}
+
+static void plan_tiles(Plan &P) {
+  choose_configs(P);
+  make_tiles(P);
+  std::vector<std::vector<int>> tile_pred;
+  build_deps(P, tile_pred);
+  if ((int)P.tiles.size() < P.grid) P.grid = std::max(1, (int)P.tiles.size());
+  order_tiles(P, tile_pred);
+  roofline(P);
+}
+
+// Host-only planning (no device): the queue-ordered tiles for a GPU of n_sm SMs
+// running one executor CTA per SM.
+extern "C" dag_status dag_plan_host(const dag_node_desc *nodes, int n_nodes, const dag_edge *edges, int n_edges,
+                                    const dag_buffer_desc *buffers, int n_buffers, const dag_options *opts, int n_sm,
+                                    int32_t *out6, int cap, int *n_tiles, dag_plan_info *info) {
+  if (!n_tiles || n_sm <= 0) return fail(DAG_EINVAL, "null n_tiles or n_sm <= 0");
+  Plan P;
+  if (opts) P.opt = *opts;
+  dag_status s = build_graph(nodes, n_nodes, edges, n_edges, buffers, n_buffers, P.g);
+  if (s) return s;
+  P.n_sm = n_sm;
+  P.grid = P.opt.max_ctas > 0 ? std::min(n_sm, P.opt.max_ctas) : n_sm;
+  plan_tiles(P);
+  const int nt = (int)P.queue.size();
+  *n_tiles = nt;
+  for (int i = 0; out6 && i < nt && i < cap; ++i) {
+    const TileDesc &t = P.queue[i];
+    const int32_t r[6] = {t.node, t.r0, t.r1, t.c0, t.c1, t.cfg};
+    memcpy(out6 + 6 * i, r, sizeof r);
+  }
+  if (info) {
+    info->n_tiles = nt;
+    info->n_counters = P.n_counters;
+    info->n_waits = (int)P.waits.size();
+    info->grid = P.grid;
+    info->smem_bytes = 0;
+    info->flops = P.flops;
+    info->bytes = P.bytes;
+    info->critical_path_us = P.cp_us;
+    info->work_bound_us = P.work_us;
+  }
+  return DAG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// handle
+// ---------------------------------------------------------------------------
+struct dag_handle {
+  Plan P;
+  int device = 0;
+  // device memory
+  void *arena = nullptr;      // buffers
+  void *meta = nullptr;       // plan arrays
+  std::vector<char *> dptr;   // per buffer (view-adjusted)
+  std::vector<int64_t> ld;    // per buffer row pitch (elements)
+  ExecParams xp{};            // persistent-mode parameters
+  TileDesc *d_coarse = nullptr;
+  TraceRec *d_trace = nullptr;
+  uint32_t *d_flags = nullptr;
+  Ctrl *d_ctrl = nullptr;
+  // host side
+  std::vector<const void *> host_in;
+  std::vector<void *> host_out;
+  std::vector<char> resident_dirty;
+  cudaStream_t up[2] = {nullptr, nullptr}, down = nullptr;
+  cudaEvent_t ev_done = nullptr, ev_read = nullptr;
+  uint32_t epoch = 0;
+  bool in_flight = false, reading = false;
+  dag_status poisoned = DAG_OK;
+  int last_mode = 0;
+};
+
+static void free_handle(dag_handle *h) {
+  if (!h) return;
+  if (h->arena) cudaFree(h->arena);
+  if (h->meta) cudaFree(h->meta);
+  for (auto &s : h->up)
+    if (s) cudaStreamDestroy(s);
+  if (h->down) cudaStreamDestroy(h->down);
+  if (h->ev_done) cudaEventDestroy(h->ev_done);
+  if (h->ev_read) cudaEventDestroy(h->ev_read);
+  delete h;
+}
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+static dag_status encode_map(CUtensorMap *m, const void *base, uint64_t d0, uint64_t d1, uint64_t d2,
+                             uint64_t stride1_bytes, uint64_t stride2_bytes, uint32_t b0, uint32_t b1) {
+  const cuuint64_t dims[3] = {d0, d1, d2};
+  const cuuint64_t strides[2] = {stride1_bytes, stride2_bytes};
+  const cuuint32_t box[3] = {b0, b1, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = p_encode_tiled(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box,
+                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(DAG_EUNSUPPORTED, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return DAG_OK;
+}
+
+extern "C" dag_status dag_create(const dag_node_desc *nodes, int n_nodes, const dag_edge *edges, int n_edges,
+                                 const dag_buffer_desc *buffers, int n_buffers, const dag_options *opts,
+                                 dag_handle **out) {
+  if (!out) return fail(DAG_EINVAL, "null output handle");
+  *out = nullptr;
+  dag_status s = init_driver();
+  if (s) return s;
+  dag_handle *h = new (std::nothrow) dag_handle();
+  if (!h) return fail(DAG_ENOMEM, "host allocation");
+  Plan &P = h->P;
+  if (opts) P.opt = *opts;
+  if (!P.opt.timeout_ns) P.opt.timeout_ns = 2000000000ull;
+  if ((s = build_graph(nodes, n_nodes, edges, n_edges, buffers, n_buffers, P.g))) { free_handle(h); return s; }
+  Graph &g = P.g;
+  if (cudaGetDevice(&h->device) != cudaSuccess) { free_handle(h); return fail(DAG_EDEVICE, "no CUDA device"); }
+  cudaDeviceGetAttribute(&P.n_sm, cudaDevAttrMultiProcessorCount, h->device);
+  const int per_sm = std::max(1, max_coresident_ctas_per_sm());
+  P.grid = P.n_sm * per_sm;
+  if (P.opt.max_ctas > 0) P.grid = std::min(P.grid, P.opt.max_ctas);
+
+  plan_tiles(P);
+
+  // ---- device buffers: one arena, row pitch a multiple of 16 elements ----
+  h->dptr.assign(g.nb, nullptr);
+  h->ld.assign(g.nb, 0);
+  std::vector<size_t> off(g.nb, 0);
+  size_t total = 0;
+  for (int b = 0; b < g.nb; ++b) {
+    if (g.bufs[b].view_of >= 0) continue;
+    h->ld[b] = round_up(g.bufs[b].cols, 16);
+    off[b] = total;
+    total = align_up(total + (size_t)g.bufs[b].rows * h->ld[b] * esize(g.bufs[b].dtype), 1024);
+  }
+  if (total && cudaMalloc(&h->arena, total) != cudaSuccess) { free_handle(h); return fail(DAG_ENOMEM, "device buffers (%zu bytes)", total); }
+  if (total) cudaMemset(h->arena, 0, total);
+  for (int b = 0; b < g.nb; ++b) {
+    const int r = g.root[b];
+    h->ld[b] = h->ld[r];
+    h->dptr[b] = (char *)h->arena + off[r] + (size_t)g.coff[b] * esize(g.bufs[b].dtype);
+  }
+
+  // ---- node parameters and tensor maps ----
+  const int nn = g.nn, nt = (int)P.tiles.size();
+  std::vector<NodeParams> np(std::max(1, nn));
+  std::vector<CUtensorMap> maps;
+  for (int v = 0; v < nn; ++v) {
+    const dag_node_desc &n = g.nodes[v];
+    NodeParams &q = np[v];
+    memset(&q, 0, sizeof q);
+    q.A = h->dptr[n.a];
+    q.lda = h->ld[n.a];
+    q.a_dt = g.bufs[n.a].dtype;
+    if (n.op == DAG_OP_GEMM || n.op == DAG_OP_ADD) { q.B = h->dptr[n.b]; q.ldb = h->ld[n.b]; q.b_dt = g.bufs[n.b].dtype; }
+    if (n.op == DAG_OP_GEMM && n.bias >= 0) { q.bias = h->dptr[n.bias]; q.bias_dt = g.bufs[n.bias].dtype; }
+    q.C = h->dptr[n.out];
+    q.ldc = h->ld[n.out];
+    q.c_dt = g.bufs[n.out].dtype;
+    q.M = g.M[v]; q.N = g.N[v]; q.K = g.K[v]; q.batch = n.op == DAG_OP_GEMM ? n.batch : 1;
+    q.trans_b = n.trans_b; q.act = n.act; q.scale = n.scale;
+    q.tmap_a = q.tmap_b = -1;
+    // 16-byte vector paths: every operand's view offset is 16-byte aligned
+    // (row pitches are multiples of 16 elements by construction)
+    bool vec = true;
+    int in[3];
+    const int k = g.inputs(v, in);
+    for (int i = 0; i < k; ++i) vec &= ((size_t)g.coff[in[i]] * esize(g.bufs[in[i]].dtype)) % 16 == 0;
+    vec &= ((size_t)g.coff[n.out] * esize(g.bufs[n.out].dtype)) % 16 == 0;
+    q.vec = vec ? 1 : 0;
+    if (n.op == DAG_OP_GEMM && q.a_dt == DAG_BF16) {
+      if (((uintptr_t)q.A % 16) || ((uintptr_t)q.B % 16)) {
+        free_handle(h);
+        return fail(DAG_EUNSUPPORTED, "node %d: bf16 GEMM operand view not 16-byte aligned", v);
+      }
+      const int M = q.M, N = q.N, K = q.K, B = n.batch;
+      CUtensorMap ma, mb;
+      if ((s = encode_map(&ma, q.A, K, M, B, q.lda * 2, (uint64_t)M * q.lda * 2, kBK, kBM))) { free_handle(h); return s; }
+      if (n.trans_b) s = encode_map(&mb, q.B, K, N, B, q.ldb * 2, (uint64_t)N * q.ldb * 2, kBK, P.cfg[v]);
+      else s = encode_map(&mb, q.B, N, K, B, q.ldb * 2, (uint64_t)K * q.ldb * 2, 64, kBK);
+      if (s) { free_handle(h); return s; }
+      q.tmap_a = (int)maps.size(); maps.push_back(ma);
+      q.tmap_b = (int)maps.size(); maps.push_back(mb);
+    }
+  }
+
+  // ---- plan arrays in one device block ----
+  std::vector<TileDesc> coarse(P.tiles);
+  size_t o_maps = 0;
+  size_t o_tiles = align_up(o_maps + maps.size() * sizeof(CUtensorMap), 256);
+  size_t o_coarse = align_up(o_tiles + (size_t)nt * sizeof(TileDesc), 256);
+  size_t o_waits = align_up(o_coarse + (size_t)nt * sizeof(TileDesc), 256);
+  size_t o_rels = align_up(o_waits + P.waits.size() * sizeof(Wait), 256);
+  size_t o_nodes = align_up(o_rels + P.rels.size() * sizeof(uint32_t), 256);
+  size_t o_cnt = align_up(o_nodes + np.size() * sizeof(NodeParams), 256);
+  size_t o_flags = align_up(o_cnt + (size_t)std::max(1, P.n_counters) * 4, 256);
+  size_t o_ctrl = align_up(o_flags + (size_t)std::max(1, P.n_flags) * 4, 256);
+  size_t o_trace = align_up(o_ctrl + sizeof(Ctrl), 256);
+  size_t mtotal = align_up(o_trace + (size_t)std::max(1, nt) * sizeof(TraceRec), 256);
+  if (cudaMalloc(&h->meta, mtotal) != cudaSuccess) { free_handle(h); return fail(DAG_ENOMEM, "plan arrays"); }
+  char *m = (char *)h->meta;
+  cudaMemset(m, 0, mtotal);
+  auto put = [&](size_t o, const void *src, size_t n) { return n ? cudaMemcpy(m + o, src, n, cudaMemcpyHostToDevice) : cudaSuccess; };
+  if (put(o_maps, maps.data(), maps.size() * sizeof(CUtensorMap)) || put(o_tiles, P.queue.data(), (size_t)nt * sizeof(TileDesc)) ||
+      put(o_coarse, coarse.data(), (size_t)nt * sizeof(TileDesc)) || put(o_waits, P.waits.data(), P.waits.size() * sizeof(Wait)) ||
+      put(o_rels, P.rels.data(), P.rels.size() * sizeof(uint32_t)) || put(o_nodes, np.data(), np.size() * sizeof(NodeParams))) {
+    free_handle(h);
+    return fail(DAG_EDEVICE, "plan upload: %s", cudaGetErrorString(cudaGetLastError()));
+  }
+  ExecParams &x = h->xp;
+  x.tiles = (const TileDesc *)(m + o_tiles);
+  x.n_tiles = nt;
+  x.mode = 0;
+  x.tile_begin = 0;
+  x.trace_on = P.opt.trace ? 1 : 0;
+  x.waits = (const Wait *)(m + o_waits);
+  x.rels = (const uint32_t *)(m + o_rels);
+  x.nodes = (const NodeParams *)(m + o_nodes);
+  x.tmaps = (const CUtensorMap *)(m + o_maps);
+  x.counters = (uint32_t *)(m + o_cnt);
+  x.flags = (uint32_t *)(m + o_flags);
+  x.ctrl = (Ctrl *)(m + o_ctrl);
+  x.trace = (TraceRec *)(m + o_trace);
+  x.timeout_ns = P.opt.timeout_ns;
+  h->d_coarse = (TileDesc *)(m + o_coarse);
+  h->d_flags = x.flags;
+  h->d_ctrl = x.ctrl;
+  h->d_trace = x.trace;
+
+  h->host_in.assign(g.nb, nullptr);
+  h->host_out.assign(g.nb, nullptr);
+  h->resident_dirty.assign(g.nb, 0);
+  for (auto &st : h->up)
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) { free_handle(h); return fail(DAG_EDEVICE, "stream"); }
+  if (cudaStreamCreateWithFlags(&h->down, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_done, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_read, cudaEventDisableTiming) != cudaSuccess) {
+    free_handle(h);
+    return fail(DAG_EDEVICE, "stream/event creation");
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) { free_handle(h); return fail(DAG_EDEVICE, "setup: %s", cudaGetErrorString(cudaGetLastError())); }
+  *out = h;
+  return DAG_OK;
+}
+
+static dag_status check_handle(dag_handle *h) {
+  if (!h) return fail(DAG_EINVAL, "null handle");
+  if (h->poisoned) return fail(h->poisoned, "handle poisoned by an earlier device error");
+  return DAG_OK;
+}
+
+extern "C" dag_status dag_set_input(dag_handle *h, int buf, const void *host_ptr) {
+  dag_status s = check_handle(h);
+  if (s) return s;
+  if (buf < 0 || buf >= h->P.g.nb || !(h->P.g.bufs[buf].flags & DAG_BUF_INPUT))
+    return fail(DAG_EINVAL, "buffer %d is not an input", buf);
+  if (h->in_flight) return fail(DAG_EBUSY, "a submit is in flight");
+  h->host_in[buf] = host_ptr;
+  if (h->P.g.bufs[buf].flags & DAG_BUF_RESIDENT) h->resident_dirty[buf] = host_ptr ? 1 : 0;
+  return DAG_OK;
+}
+
+extern "C" dag_status dag_set_output(dag_handle *h, int buf, void *host_ptr) {
+  dag_status s = check_handle(h);
+  if (s) return s;
+  if (buf < 0 || buf >= h->P.g.nb) return fail(DAG_EINVAL, "bad buffer %d", buf);
+  if (h->in_flight) return fail(DAG_EBUSY, "a submit is in flight");
+  h->host_out[buf] = host_ptr;
+  return DAG_OK;
+}
+
+static cudaError_t copy_h2d(dag_handle *h, int b, cudaStream_t st) {
+  const dag_buffer_desc &d = h->P.g.bufs[b];
+  const size_t w = (size_t)d.cols * esize(d.dtype);
+  return cudaMemcpy2DAsync(h->dptr[b], (size_t)h->ld[b] * esize(d.dtype), h->host_in[b], w, w, d.rows,
+                           cudaMemcpyHostToDevice, st);
+}
+
+static dag_status enqueue_readbacks(dag_handle *h, cudaStream_t stream) {
+  h->reading = false;
+  for (int b = 0; b < h->P.g.nb; ++b) {
+    if (!h->host_out[b]) continue;
+    if (!h->reading) {
+      CUDA_TRY(cudaStreamWaitEvent(h->down, h->ev_done, 0));
+      h->reading = true;
+    }
+    const dag_buffer_desc &d = h->P.g.bufs[b];
+    const size_t w = (size_t)d.cols * esize(d.dtype);
+    CUDA_TRY(cudaMemcpy2DAsync(h->host_out[b], w, h->dptr[b], (size_t)h->ld[b] * esize(d.dtype), w, d.rows,
+                               cudaMemcpyDeviceToHost, h->down));
+  }
+  if (h->reading) CUDA_TRY(cudaEventRecord(h->ev_read, h->down));
+  (void)stream;
+  return DAG_OK;
+}
+
+extern "C" dag_status dag_submit(dag_handle *h, void *stream_) {
+  dag_status s = check_handle(h);
+  if (s) return s;
+  if (h->in_flight) return fail(DAG_EBUSY, "previous submit not waited for");
+  cudaStream_t stream = (cudaStream_t)stream_;
+  Plan &P = h->P;
+  // resident inputs that changed: uploaded in stream order before the launch
+  for (int b = 0; b < P.g.nb; ++b)
+    if (h->resident_dirty[b]) {
+      CUDA_TRY(copy_h2d(h, b, stream));
+      h->resident_dirty[b] = 0;
+    }
+  // streamed inputs: copy on an upload stream, then raise the ready flag;
+  // tiles that read the buffer acquire the flag (the copy engine overlaps compute)
+  const uint32_t want = h->epoch + 1;
+  int k = 0;
+  for (int b = 0; b < P.g.nb; ++b) {
+    const int f = P.flag_of_root[b];
+    if (f < 0) continue;
+    CUdeviceptr flag = (CUdeviceptr)(h->d_flags + f);
+    if (h->host_in[b]) {
+      cudaStream_t st = h->up[k++ & 1];
+      CUDA_TRY(copy_h2d(h, b, st));
+      if (p_write_value32((CUstream)st, flag, want, CU_STREAM_WRITE_VALUE_DEFAULT) != CUDA_SUCCESS)
+        return fail(DAG_EDEVICE, "cuStreamWriteValue32");
+    } else if (p_write_value32((CUstream)stream, flag, want, CU_STREAM_WRITE_VALUE_DEFAULT) != CUDA_SUCCESS) {
+      return fail(DAG_EDEVICE, "cuStreamWriteValue32");
+    }
+  }
+  if (P.tiles.size()) CUDA_TRY(launch_persistent(h->xp, P.grid, stream));
+  CUDA_TRY(cudaEventRecord(h->ev_done, stream));
+  if ((s = enqueue_readbacks(h, stream))) return s;
+  h->epoch++;
+  h->in_flight = true;
+  h->last_mode = 0;
+  return DAG_OK;
+}
+
+extern "C" dag_status dag_submit_coarse(dag_handle *h, void *stream_) {
+  dag_status s = check_handle(h);
+  if (s) return s;
+  if (h->in_flight) return fail(DAG_EBUSY, "previous submit not waited for");
+  cudaStream_t stream = (cudaStream_t)stream_;
+  Plan &P = h->P;
+  for (int b = 0; b < P.g.nb; ++b) {
+    if (h->resident_dirty[b]) { CUDA_TRY(copy_h2d(h, b, stream)); h->resident_dirty[b] = 0; }
+    else if (P.flag_of_root[b] >= 0 && h->host_in[b]) CUDA_TRY(copy_h2d(h, b, stream));
+  }
+  ExecParams x = h->xp;
+  x.tiles = h->d_coarse;
+  for (int v : P.g.topo)
+    if (P.node_count[v]) CUDA_TRY(launch_coarse(x, P.node_first[v], P.node_count[v], stream));
+  CUDA_TRY(cudaEventRecord(h->ev_done, stream));
+  if ((s = enqueue_readbacks(h, stream))) return s;
+  h->in_flight = true;
+  h->last_mode = 1;
+  return DAG_OK;
+}
+
+static dag_status poll_event(cudaEvent_t ev, uint64_t timeout_ns) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (uint64_t n = 0;; ++n) {
+    cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) return DAG_OK;
+    if (e != cudaErrorNotReady) return fail(DAG_EDEVICE, "device error: %s", cudaGetErrorString(e));
+    if ((uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now() - t0).count() > timeout_ns)
+      return fail(DAG_ETIMEOUT, "dag_wait timed out");
+    if (n > 2000) std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+}
+
+extern "C" dag_status dag_wait(dag_handle *h, uint64_t timeout_ns) {
+  if (!h) return fail(DAG_EINVAL, "null handle");
+  if (h->poisoned) return fail(h->poisoned, "handle poisoned by an earlier device error");
+  if (!h->in_flight) return DAG_OK;
+  dag_status s = poll_event(h->reading ? h->ev_read : h->ev_done, timeout_ns ? timeout_ns : ~0ull);
+  if (s == DAG_ETIMEOUT) return s;
+  h->in_flight = false;
+  if (s) { h->poisoned = s; return s; }
+  Ctrl c;
+  if (cudaMemcpy(&c, h->d_ctrl, sizeof c, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    h->poisoned = DAG_EDEVICE;
+    return fail(DAG_EDEVICE, "reading the device error word");
+  }
+  if (c.err_code) {
+    h->poisoned = c.err_code == E_DEP_TIMEOUT || c.err_code == E_PIPE_TIMEOUT ? DAG_ETIMEOUT : DAG_EDEVICE;
+    return fail(h->poisoned, "device error %u at tile %u", c.err_code, c.err_tile);
+  }
+  return DAG_OK;
+}
+
+extern "C" dag_status dag_get_output(dag_handle *h, int buf, void *host_ptr) {
+  dag_status s = check_handle(h);
+  if (s) return s;
+  if (buf < 0 || buf >= h->P.g.nb || !host_ptr) return fail(DAG_EINVAL, "bad buffer or pointer");
+  if (h->in_flight) return fail(DAG_EBUSY, "call dag_wait first");
+  const dag_buffer_desc &d = h->P.g.bufs[buf];
+  const size_t w = (size_t)d.cols * esize(d.dtype);
+  CUDA_TRY(cudaMemcpy2D(host_ptr, w, h->dptr[buf], (size_t)h->ld[buf] * esize(d.dtype), w, d.rows, cudaMemcpyDeviceToHost));
+  return DAG_OK;
+}
+
+extern "C" const void *dag_device_ptr(dag_handle *h, int buf, int64_t *ld_elems) {
+  if (!h || buf < 0 || buf >= h->P.g.nb) return nullptr;
+  if (ld_elems) *ld_elems = h->ld[buf];
+  return h->dptr[buf];
+}
+
+extern "C" dag_status dag_destroy(dag_handle *h) {
+  if (!h) return DAG_OK;
+  if (h->in_flight && !h->poisoned) poll_event(h->reading ? h->ev_read : h->ev_done, 10ull * 1000000000ull);
+  free_handle(h);
+  return DAG_OK;
+}
+
+extern "C" void *dag_host_alloc(size_t bytes) {
+  void *p = nullptr;
+  if (cudaHostAlloc(&p, bytes ? bytes : 1, cudaHostAllocDefault) != cudaSuccess) {
+    fail(DAG_ENOMEM, "cudaHostAlloc(%zu)", bytes);
+    return nullptr;
+  }
+  return p;
+}
+
+extern "C" void dag_host_free(void *p) {
+  if (p) cudaFreeHost(p);
+}
+
+extern "C" dag_status dag_trace_get(dag_handle *h, dag_trace_record *out, int cap, int *n) {
+  if (!h || !n) return fail(DAG_EINVAL, "null argument");
+  if (h->in_flight) return fail(DAG_EBUSY, "call dag_wait first");
+  const int nt = (int)h->P.tiles.size();
+  *n = nt;
+  if (!out || cap <= 0) return DAG_OK;
+  if (!h->P.opt.trace) return fail(DAG_EINVAL, "tracing was not enabled in dag_options");
+  std::vector<TraceRec> tr(nt);
+  if (nt) CUDA_TRY(cudaMemcpy(tr.data(), h->d_trace, (size_t)nt * sizeof(TraceRec), cudaMemcpyDeviceToHost));
+  const std::vector<TileDesc> &src = h->last_mode == 0 ? h->P.queue : h->P.tiles;
+  for (int i = 0; i < nt && i < cap; ++i) {
+    const TileDesc &t = src[i];
+    out[i] = dag_trace_record{t.node, t.r0, t.r1, t.c0, t.c1, tr[i].start_ticket, tr[i].end_ticket, tr[i].smid,
+                              tr[i].t_start, tr[i].t_end};
+  }
+  return DAG_OK;
+}
+
+extern "C" dag_status dag_plan_get(dag_handle *h, dag_plan_info *o) {
+  if (!h || !o) return fail(DAG_EINVAL, "null argument");
+  o->n_tiles = (int)h->P.tiles.size();
+  o->n_counters = h->P.n_counters;
+  o->n_waits = (int)h->P.waits.size();
+  o->grid = h->P.grid;
+  o->smem_bytes = exec_smem_bytes();
+  o->flops = h->P.flops;
+  o->bytes = h->P.bytes;
+  o->critical_path_us = h->P.cp_us;
+  o->work_bound_us = h->P.work_us;
+  return DAG_OK;
+}
+
+extern "C" dag_status dag_tiles_get(dag_handle *h, int32_t *out6, int cap, int *n) {
+  if (!h || !n) return fail(DAG_EINVAL, "null argument");
+  const int nt = (int)h->P.queue.size();
+  *n = nt;
+  for (int i = 0; out6 && i < nt && i < cap; ++i) {
+    const TileDesc &t = h->P.queue[i];
+    const int32_t r[6] = {t.node, t.r0, t.r1, t.c0, t.c1, t.cfg};
+    memcpy(out6 + 6 * i, r, sizeof r);
+  }
+  return DAG_OK;
+}

@@ -1,0 +1,200 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Sizes here span several tiles with ragged tails; the full workload sizes are
+in test_gpu_full.py.  Tolerances (normwise per buffer): 1e-5 for f32 nodes,
+2e-2 for bf16-input / f32-accumulate nodes.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_2009_07482_gb300 import _binding as abi
+from paper_2009_07482_gb300.dag import Dag, options
+from synth import BF16, F32
+from synth.workloads import Workload, branchy_mlp, encoder_block, fork_join, random_layered
+from tests.gpu_util import bits_equal, check_trace, compare, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    from paper_2009_07482_gb300 import build
+    build.build()
+    abi.lib()
+
+
+def _roundtrip(w, opts=None, coarse_too=True):
+    ins = w.make_inputs()
+    ref = oracle.run(w, ins)
+    d = Dag(w, opts or options(trace=1))
+    d.set_inputs(ins)
+    d.run()
+    got = {b: d.output(b) for b in sorted({n.out for n in w.nodes})}
+    errs = compare(w, got, ref)
+    check_trace(w, d)
+    if coarse_too:
+        d.run(coarse=True)
+        got_c = {b: d.output(b) for b in got}
+        assert bits_equal(got, got_c), "coarse and fine paths differ"
+    d.close()
+    return errs
+
+
+@pytest.mark.parametrize("n", [256, 200, 64, 130])
+def test_fork_join_f32(n):
+    _roundtrip(fork_join(n, seed=n))
+
+
+def test_fork_join_bf16():
+    _roundtrip(fork_join(256, dtype=BF16))
+
+
+def _gemm_case(M, N, K, dt, trans_b=0, batch=1, bias=True, act="none", out_dt=F32, scale=1.0, seed=0):
+    w = Workload(f"gemm_{M}x{N}x{K}_{dt}_t{trans_b}_b{batch}")
+    A = w.buf(batch * M, K, dt, "input", ("uniform", seed + 1))
+    B = w.buf(batch * N if trans_b else batch * K, K if trans_b else N, dt, "input", ("uniform", seed + 2))
+    bb = w.buf(1, N, F32, "input", ("normal", seed + 3, 0.5)) if bias else -1
+    C = w.buf(batch * M, N, out_dt, "output")
+    w.node("gemm", A, C, b=B, bias=bb, trans_b=trans_b, batch=batch, act=act, scale=scale)
+    return w
+
+
+GEMM_CASES = [
+    dict(M=256, N=256, K=256, dt=BF16),
+    dict(M=300, N=200, K=130, dt=BF16),                       # ragged M, N, K
+    dict(M=128, N=64, K=64, dt=BF16, trans_b=1),
+    dict(M=256, N=512, K=320, dt=BF16, trans_b=1, act="relu"),
+    dict(M=100, N=96, K=72, dt=BF16, batch=3),                # batched, ragged per batch
+    dict(M=64, N=128, K=200, dt=BF16, batch=4, trans_b=1, act="gelu", out_dt=BF16),
+    dict(M=512, N=1024, K=512, dt=BF16, act="gelu", out_dt=BF16, scale=0.5),
+    dict(M=256, N=256, K=256, dt=F32),
+    dict(M=300, N=200, K=130, dt=F32, act="relu"),
+    dict(M=100, N=96, K=72, dt=F32, batch=3, trans_b=1),
+    dict(M=77, N=33, K=19, dt=F32, act="gelu", out_dt=BF16),
+]
+
+
+@pytest.mark.parametrize("case", GEMM_CASES, ids=lambda c: "-".join(f"{k}{v}" for k, v in c.items()))
+def test_gemm(case):
+    _roundtrip(_gemm_case(**case))
+
+
+@pytest.mark.parametrize("bn", [64, 128, 256])
+@pytest.mark.parametrize("trans_b", [0, 1])
+def test_gemm_bf16_every_tile_width(bn, trans_b):
+    w = _gemm_case(384, 640, 448, BF16, trans_b=trans_b, act="relu")
+    _roundtrip(w, options(trace=1, tile_override=bn), coarse_too=False)
+
+
+@pytest.mark.parametrize("N,dt_in,dt_out,scale", [(256, F32, BF16, 0.125), (1000, F32, F32, 1.0),
+                                                  (2048, BF16, F32, 0.5), (33, BF16, BF16, 2.0)])
+def test_softmax(N, dt_in, dt_out, scale):
+    w = Workload("softmax")
+    x = w.buf(300, N, dt_in, "input", ("uniform", 5))
+    s = w.buf(300, N, dt_in, name="xs")
+    y = w.buf(300, N, dt_out, "output")
+    w.node("unary", x, s)          # routes the input through a producer tile
+    w.node("softmax", s, y, scale=scale * 8)
+    _roundtrip(w)
+
+
+@pytest.mark.parametrize("cols", [2048, 1001, 8, 3])
+@pytest.mark.parametrize("dt", [F32, BF16])
+def test_eltwise(cols, dt):
+    w = Workload("elt")
+    a = w.buf(70, cols, dt, "input", ("uniform", 1))
+    b = w.buf(70, cols, F32, "input", ("uniform", 2))
+    c = w.buf(70, cols, dt, name="c")
+    y = w.buf(70, cols, F32, "output")
+    w.node("add", a, c, b=b, act="relu")
+    w.node("unary", c, y, act="gelu")
+    _roundtrip(w)
+
+
+@pytest.mark.parametrize("dt", [F32, BF16])
+def test_branchy_mlp_small(dt):
+    _roundtrip(branchy_mlp(dt, batch=200, width=256, hidden=512, out=128, seed=7))
+
+
+def test_encoder_small():
+    _roundtrip(encoder_block(batch=2, seq=128, d_model=256, heads=4, d_head=64, ffn=512, seed=9))
+
+
+@pytest.mark.parametrize("seed", [1000, 1001, 1002, 1003])
+def test_random_layered_small(seed):
+    _roundtrip(random_layered(seed, 6, 16, 4, sizes=(64, 128, 256)))
+
+
+def test_schedules_and_grid_sizes_give_identical_bits():
+    """No reduction is split across tiles, so every legal schedule gives the same bits."""
+    w = encoder_block(batch=2, seq=128, d_model=256, heads=4, d_head=64, ffn=512, seed=11)
+    ins = w.make_inputs()
+    base = run_gpu(w, ins)
+    for o in (options(scheduler=abi.DAG_SCHED_FIFO), options(max_ctas=1), options(max_ctas=7),
+              options(scheduler=abi.DAG_SCHED_FIFO, max_ctas=3)):
+        assert bits_equal(base, run_gpu(w, ins, opts=o))
+
+
+def test_streamed_inputs_and_repeated_submits():
+    """Inputs uploaded on the copy streams each submit (ready flags) give the
+    same bits as resident inputs, over several submits (epoch counters)."""
+    w = branchy_mlp(BF16, batch=128, width=256, hidden=256, out=128, seed=3)
+    ins = w.make_inputs()
+    base = run_gpu(w, ins, resident=True)
+    d = Dag(w)
+    d.set_inputs(ins)
+    for _ in range(3):
+        d.run()
+        assert bits_equal(base, {b: d.output(b) for b in base})
+    # new data in the streamed input changes the result; the old data restores it
+    X = w.input_ids()[0]
+    ins2 = dict(ins)
+    ins2[X] = synth.to_storage(synth.uniform(99, (128, 256)), BF16)
+    d.set_inputs({X: ins2[X]})
+    d.run()
+    ref2 = oracle.run(w, ins2)
+    compare(w, {b: d.output(b) for b in base}, ref2)
+    d.set_inputs({X: ins[X]}, pinned=True)
+    d.run()
+    assert bits_equal(base, {b: d.output(b) for b in base})
+    d.close()
+
+
+def test_device_wait_timeout_reports_and_context_survives():
+    """A tile waiting on a counter nothing releases gives up after the limit;
+    dag_wait reports DAG_ETIMEOUT, the handle is poisoned, and the GPU context
+    stays usable for a fresh DAG."""
+    w = fork_join(64)
+    ins = w.make_inputs()
+    d = Dag(w, options(timeout_ns=50_000_000, debug_never_ready=1))
+    d.set_inputs(ins)
+    d.submit()
+    st = d.wait(10_000_000_000)
+    assert st == abi.DAG_ETIMEOUT
+    with pytest.raises(abi.DagError):
+        d.submit()
+    d.close()
+    got = run_gpu(w, ins)
+    compare(w, got, oracle.run(w, ins))
+
+
+def test_empty_and_degenerate_dags():
+    w = Workload("one_elem")
+    a = w.buf(1, 1, F32, "input", ("array", [[2.0]]))
+    b = w.buf(1, 1, F32, "input", ("array", [[-3.0]]))
+    y = w.buf(1, 1, F32, "output")
+    w.node("gemm", a, y, b=b, act="relu")
+    _roundtrip(w)
+    w = Workload("single_row_softmax")
+    x = w.buf(1, 1, F32, "input", ("array", [[5.0]]))
+    y = w.buf(1, 1, F32, "output")
+    w.node("softmax", x, y)
+    _roundtrip(w)
+    # a DAG with no kernels: submit and wait are no-ops
+    w = Workload("empty")
+    w.buf(4, 4, F32, "input", ("uniform", 1))
+    d = Dag(w)
+    d.run()
+    d.close()
