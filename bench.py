@@ -1,0 +1,389 @@
+#!/usr/bin/env python3
+"""Benchmark: DAG makespan and DAGs/s of the fine-grained persistent executor.
+
+Default workload: the branchy MLP inference DAG (batch 512, four branches of
+three Linear(2048,2048)+bias+ReLU layers, pairwise add tree, Linear(2048,4096)
++ReLU, Linear(4096,1024)), bf16 inputs with f32 accumulation, synthetic seeded
+inputs.  One step = one submission of the whole DAG (one persistent kernel
+launch), weights and activations resident in HBM; L2 is flushed (a 256 MiB
+write) between timed steps, outside the timed events.
+
+Also measured and reported on the same JSON line:
+  coarse     the same tiles launched kernel by kernel on one stream
+  e2e        the same metric through the C ABI with host buffers: upload of X
+             from pinned memory, execution, readback of Y, every step
+  roofline   the executor kernel's achieved TFLOP/s against the measured peak
+  cp_roofline  makespan against the DAG's critical-path / total-work bounds
+  cpu_baseline the FP64 oracle on a bounded row sample, on the host cores
+
+--impl reference times the FP64 oracle (the only reference implementation of
+this method) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DAGs/s (fine-grained persistent executor, device makespan)"
+UNIT = "DAGs/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mlp_bf16",
+                    choices=["mlp_bf16", "mlp_f32", "fork_join", "encoder"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="few steps, no side measurements (for ncu)")
+    return ap.parse_args()
+
+
+def make_workload(name):
+    from synth.workloads import branchy_mlp, encoder_block, fork_join
+    if name == "mlp_bf16":
+        return branchy_mlp("bf16"), ("branchy MLP inference DAG, bf16 in / f32 accumulate: batch 512, 4 branches x 3 "
+                                     "Linear(2048,2048)+bias+ReLU, add tree, Linear(2048,4096)+ReLU, Linear(4096,1024)")
+    if name == "mlp_f32":
+        return branchy_mlp("f32"), "branchy MLP inference DAG, f32: batch 512, widths as mlp_bf16"
+    if name == "fork_join":
+        return fork_join(256), "fork-join DAG (paper Fig. 1): 3 GEMMs 256^3 f32 + add"
+    return encoder_block(), ("transformer encoder block DAG: 8 x 256 tokens, d_model 1024, 16 heads as fork "
+                             "branches, out proj, FFN 4096 GELU; bf16 in / f32 accumulate")
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample (rows of the batch are independent in the MLP
+# and fork-join DAGs; a sequence is independent in the encoder)
+# ---------------------------------------------------------------------------
+_INPUTS = {}
+
+
+def _oracle_seconds(w, ins, repeat=1):
+    import oracle
+    t0 = time.perf_counter()
+    for _ in range(repeat):
+        oracle.run(w, ins)
+    return (time.perf_counter() - t0) / repeat
+
+
+def oracle_model(workload, ra=4, rb=12):
+    """Seconds per full DAG of the FP64 oracle on one host core, from a bounded
+    sample.  MLP / fork-join rows are independent, so the time is
+    fixed + rows * slope (the fixed part widens each weight once); two row
+    counts give both terms.  The encoder's sequences are independent: one
+    sequence, times 8."""
+    import oracle
+    from synth.workloads import branchy_mlp, encoder_block, fork_join
+    oracle.build()
+    if workload.startswith("mlp"):
+        dt = "bf16" if workload == "mlp_bf16" else "f32"
+        wa, wb = branchy_mlp(dt, batch=ra), branchy_mlp(dt, batch=rb)
+        ta = _oracle_seconds(wa, wa.make_inputs(_INPUTS))
+        tb = _oracle_seconds(wb, wb.make_inputs(_INPUTS))
+        slope = max(tb - ta, 0.0) / (rb - ra)
+        full = ta + (512 - ra) * slope
+        desc = (f"branchy MLP {dt} on {ra} and {rb} of 512 batch rows (all 17 kernels; {ta:.2f} s, {tb:.2f} s), "
+                f"extrapolated linearly in rows to 512")
+        return full, desc, (wa, ra, ta, slope)
+    if workload == "fork_join":
+        w = fork_join(256)
+        t = _oracle_seconds(w, w.make_inputs(), repeat=3)
+        return t, "fork-join 256^3 f32: the whole DAG, mean of 3 runs", (w, 256, t, 0.0)
+    w = encoder_block(batch=1)
+    t = _oracle_seconds(w, w.make_inputs())
+    return 8 * t, f"encoder block: 1 of 8 independent sequences (all 99 kernels, {t:.2f} s), times 8", (w, 1, t, 0.0)
+
+
+def oracle_sample(workload):
+    full, desc, _ = oracle_model(workload)
+    return {"value": 1.0 / full, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+
+
+def run_reference(args):
+    """The FP64 oracle as the reference arm: each step runs a bounded sample of
+    the workload on one host core and is scaled to one full DAG with the
+    calibration of oracle_model (measured once before the steps)."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    _, desc = make_workload(args.workload)
+    full, cal_desc, (w, rows, t_cal, slope) = oracle_model(args.workload)
+    if args.workload.startswith("mlp"):
+        from synth.workloads import branchy_mlp
+        rows = 1
+        w = branchy_mlp("bf16" if args.workload == "mlp_bf16" else "f32", batch=rows)
+    ins = w.make_inputs(_INPUTS)
+    scale_rows = 512 if args.workload.startswith("mlp") else None
+    per = []
+    for i in range(args.warmup + args.steps):
+        t = _oracle_seconds(w, ins)
+        if scale_rows:
+            t = t + (scale_rows - rows) * slope
+        elif args.workload == "encoder":
+            t = 8 * t
+        if i >= args.warmup:
+            per.append(t)
+    ms = statistics.mean(per) * 1e3
+    what = f"{rows} batch row(s)" if scale_rows else cal_desc.split(" (")[0]
+    sample = f"each step: the oracle on {what}, scaled to one full DAG; calibration: {cal_desc}"
+    line = {"impl": "reference", "metric": METRIC, "value": 1e3 / ms, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+            "config": {"workload": desc, "parallelism": "host oracle, rank 0 only"},
+            "cpu_baseline": {"value": 1e3 / ms, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": 1e3 / ms, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        time.sleep(0.15)
+        self.t0 = time.time()
+        return self
+
+    def __exit__(self, *a):
+        self.t1 = time.time()
+        time.sleep(0.1)
+        self.out = ""
+        if self.p:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                self.out = ""
+
+    def summary(self):
+        sm, mx, reasons = [], 0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        import datetime
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 10:
+                continue
+            try:
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                if not (self.t0 - 0.06 <= ts <= self.t1 + 0.06):
+                    continue
+                sm.append(float(f[2]))
+                mx = max(mx, float(f[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[6:10]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def traffic_for(workload):
+    """DRAM bytes per executor launch from the committed ncu summary, if it was
+    taken on the current kernel sources (else None)."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2009_07482_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    sha = h.hexdigest()[:16]
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if os.path.exists(p):
+        for line in open(p):
+            f = line.split()
+            if len(f) >= 3 and f[0] == workload and f[1] == sha:
+                return float(f[2]), sha
+    return None, sha
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2009_07482_gb300 import _binding as abi
+    from paper_2009_07482_gb300 import build as libbuild
+    from paper_2009_07482_gb300.dag import Dag, options
+    libbuild.build()
+    abi.dag_set_device(local)
+    peaks, peaks_src = load_peaks()
+    abi.dag_set_peaks(peaks["bf16_tflops"], 0.0, peaks["hbm_gbs"])
+
+    w, desc = make_workload(args.workload)
+    ins = w.make_inputs(_INPUTS)
+    X = w.input_ids()[0]
+    Y = w.output_ids()[0]
+    # device-resident run: every input resident
+    d = Dag(w, options(), resident_inputs=True)
+    d.set_inputs(ins)
+    d.run()
+    info = d.plan()
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def timed(submit, steps, warmup):
+        for _ in range(warmup):
+            submit(sp)
+            abi.check(d.wait(), "wait")
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        barrier()
+        t0 = time.perf_counter()
+        for a, b in evs:
+            flush.zero_()
+            a.record(stream)
+            submit(sp)
+            b.record(stream)
+            abi.check(d.wait(), "wait")
+        barrier()
+        wall = time.perf_counter() - t0
+        return [a.elapsed_time(b) * 1e3 for a, b in evs], wall  # us
+
+    launches_per_step = 1
+    with ClockSampler(local) as clk:
+        fine_us, wall = timed(d.submit, args.steps, max(3, args.warmup))
+    if args.profile:
+        print(json.dumps({"profile_run": True, "median_us": statistics.median(fine_us)}))
+        d.close()
+        return 0
+    coarse_us, _ = timed(d.submit_coarse, max(10, args.steps // 4), 3)
+    n_coarse_launches = sum(1 for _ in w.nodes)
+
+    # max over ranks of the mean step time
+    mean_us = statistics.mean(fine_us)
+    if world > 1:
+        t = torch.tensor([mean_us], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        mean_us = float(t.item())
+    value = world * 1e6 / mean_us
+    med = statistics.median(fine_us)
+    q = np.percentile(fine_us, [10, 90])
+    cmed = statistics.median(coarse_us)
+
+    # e2e: host buffers through the C ABI (X streamed from pinned memory, Y read back)
+    d.close()
+    e = Dag(w, options(), streamed={X})
+    e.set_inputs({k: v for k, v in ins.items() if k != X})
+    e.run()
+    e.set_inputs({X: ins[X]}, pinned=True)
+    ybytes = w.buffers[Y].rows * w.buffers[Y].cols * (4 if w.buffers[Y].dtype == "f32" else 2)
+    ypin = abi.dag_host_alloc(ybytes)
+    abi.dag_set_output(e.h, Y, ypin)
+    for _ in range(max(3, args.warmup)):
+        e.submit(sp)
+        abi.check(e.wait(), "wait")
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e.submit(sp)
+        abi.check(e.wait(), "wait")
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    xbytes = ins[X].nbytes
+    abi.dag_set_output(e.h, Y, None)
+    abi.dag_host_free(ypin)
+    e.close()
+
+    # roofline of the executor kernel (the only kernel of a step)
+    bf16 = "bf16" in args.workload or args.workload == "encoder"
+    if bf16:
+        peak = peaks["bf16_tflops"]
+        achieved = info.flops / (mean_us * 1e-6) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": f"{peaks_src} bf16 burst (MEASURED_PEAKS.json)" if peaks_src == "measured" else "fallback"}
+    else:
+        # f32 GEMMs on the FP32 ALUs: peak = 152 SMs x 128 FFMA/clk x 2 x max clock
+        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        achieved = info.flops / (mean_us * 1e-6) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": "derived: 152 SMs x 128 f32 FMA/clk x 2 flop x max SM clock"}
+    traffic, sha = traffic_for(args.workload)
+    roof["traffic"] = traffic
+    roof["algorithmic"] = {"flops_per_launch": info.flops, "bytes_per_launch": info.bytes}
+    roof["kernel"] = "dagx::dag_exec_kernel"
+    roof["kernel_src_sha"] = sha
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mean_us / 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16" if bf16 else "f32", "data": "synthetic (seeded SplitMix64)",
+        "config": {"workload": desc, "nodes": len(w.nodes), "tiles": info.n_tiles, "grid": info.grid,
+                   "l2": "flushed between steps (256 MiB write outside the timed events)",
+                   "parallelism": f"replicas x{world} (independent DAGs per GPU)" if world > 1 else "1 GPU"},
+        "makespan_us": {"median": med, "p10": float(q[0]), "p90": float(q[1]), "mean": statistics.mean(fine_us)},
+        "coarse": {"median_us": cmed, "launches_per_step": n_coarse_launches,
+                   "speedup_fine_over_coarse": cmed / med},
+        "cp_roofline": {"critical_path_us": info.critical_path_us, "work_bound_us": info.work_bound_us,
+                        "frac_of_cp": info.critical_path_us / med, "frac_of_work_bound": info.work_bound_us / med},
+        "roofline": roof,
+        "e2e": {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(xbytes),
+                "d2h_bytes_per_step": int(ybytes), "ms_per_step": e2e_s * 1e3},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(args.workload)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -190,6 +190,12 @@ dag_status dag_destroy(dag_handle *h);
 /* dag_last_error: message of the last failure on this thread ("" if none). */
 const char *dag_last_error(void);
 
+/* dag_set_device: make CUDA device `ordinal` current for the calling host
+ * thread inside the library (the library links its own CUDA runtime, so a
+ * device chosen through another runtime instance does not carry over).
+ * Handles created afterwards on this thread live on that device. */
+dag_status dag_set_device(int ordinal);
+
 /* pinned host memory for asynchronous uploads/readbacks */
 void *dag_host_alloc(size_t bytes);
 void dag_host_free(void *p);
@@ -230,18 +236,26 @@ dag_status dag_analyze(const dag_node_desc *nodes, int n_nodes, const dag_edge *
 
 /* One executed tile: output region of one kernel, with the tickets it drew
  * from one global counter after acquiring its inputs (start) and after
- * writing its output, before releasing it (end), %globaltimer times (ns) and
- * the SM it ran on. */
+ * writing its output, before releasing it (end), %globaltimer times (ns) of
+ * the claim of its queue position, the end of its waits, the start of its
+ * epilogue / SIMT work and its release, and the SM it ran on. */
 typedef struct {
   int32_t node, r0, r1, c0, c1;   /* region of the kernel's output buffer */
   uint32_t start_ticket, end_ticket;
   uint32_t smid;
-  uint64_t t_start_ns, t_end_ns;
+  uint64_t t_claim_ns, t_start_ns, t_work_ns, t_end_ns;
 } dag_trace_record;
 
 /* dag_trace_get: records of the last submit in queue order (needs
  * opts.trace; call after dag_wait); *n = number of tiles. */
 dag_status dag_trace_get(dag_handle *h, dag_trace_record *out, int cap, int *n);
+
+/* dag_trace_stamps: per tile (queue order of the last submit), ten
+ * %globaltimer stamps (ns): claim, dependencies satisfied, last operand load
+ * issued, first MMA, last MMA committed, workers start, accumulator ready,
+ * stores issued, fence and barrier done, release done (0 where a phase does
+ * not apply).  out holds 10 * cap values.  Diagnostic; needs opts.trace. */
+dag_status dag_trace_stamps(dag_handle *h, uint64_t *out, int cap, int *n);
 
 /* Static plan facts. */
 typedef struct {

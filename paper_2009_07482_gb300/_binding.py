@@ -64,7 +64,7 @@ class dag_analysis(C.Structure):
 
 class dag_trace_record(C.Structure):
     _fields_ = [("node", i32), ("r0", i32), ("r1", i32), ("c0", i32), ("c1", i32), ("start_ticket", u32),
-                ("end_ticket", u32), ("smid", u32), ("t_start_ns", u64), ("t_end_ns", u64)]
+                ("end_ticket", u32), ("smid", u32), ("t_claim_ns", u64), ("t_start_ns", u64), ("t_work_ns", u64), ("t_end_ns", u64)]
 
 
 class dag_plan_info(C.Structure):
@@ -105,6 +105,8 @@ _SIGS = {
                             C.POINTER(dag_buffer_desc), C.c_int, C.POINTER(dag_options), C.c_int,
                             C.POINTER(i32), C.c_int, C.POINTER(C.c_int), C.POINTER(dag_plan_info)]),
     "dag_set_peaks": (None, [C.c_double, C.c_double, C.c_double]),
+    "dag_set_device": (i32, [C.c_int]),
+    "dag_trace_stamps": (i32, [C.c_void_p, C.POINTER(u64), C.c_int, C.POINTER(C.c_int)]),
 }
 
 
@@ -233,6 +235,16 @@ def dag_trace_get(h):
     return recs[: n.value]
 
 
+def dag_trace_stamps(h):
+    """(n_tiles, 10) uint64 array of per-phase %globaltimer stamps (see dagexec.h)."""
+    import numpy as np
+    n = C.c_int(0)
+    check(lib().dag_trace_stamps(h, None, 0, C.byref(n)), "dag_trace_stamps")
+    out = (u64 * (10 * max(1, n.value)))()
+    check(lib().dag_trace_stamps(h, out, n.value, C.byref(n)), "dag_trace_stamps")
+    return np.frombuffer(out, dtype=np.uint64)[: 10 * n.value].reshape(-1, 10).copy()
+
+
 def dag_plan_get(h) -> dag_plan_info:
     info = dag_plan_info()
     check(lib().dag_plan_get(h, C.byref(info)), "dag_plan_get")
@@ -246,6 +258,10 @@ def dag_tiles_get(h):
     out = (i32 * (6 * max(1, n.value)))()
     check(lib().dag_tiles_get(h, out, n.value, C.byref(n)), "dag_tiles_get")
     return np.frombuffer(out, dtype=np.int32)[: 6 * n.value].reshape(-1, 6).copy()
+
+
+def dag_set_device(ordinal: int) -> None:
+    check(lib().dag_set_device(ordinal), "dag_set_device")
 
 
 def dag_set_peaks(bf16_tflops: float, f32_tflops: float, hbm_gbs: float) -> None:

@@ -19,14 +19,21 @@ enum TileOp : int32_t {
 // f32 SIMT GEMM tile shapes (cfg field of a T_GEMM_F32 tile)
 enum F32Cfg : int32_t { F32_64x64 = 0, F32_128x64 = 1, F32_128x128 = 2 };
 
-constexpr int kThreads = 256;       // 8 warps per CTA
+// CTA layout: warp 0 = scheduler + TMA producer, warp 1 = MMA issuer,
+// warps 2-3 idle, warps 4-11 = 256 worker threads (GEMM epilogues and every
+// SIMT tile).
+constexpr int kThreads = 384;
+constexpr int kWorkerBase = 128;    // first worker thread
+constexpr int kWorkers = 256;       // worker threads
 constexpr int kBM = 128;            // bf16 GEMM tile rows (MMA M)
 constexpr int kBK = 64;             // bf16 K per stage (one 128-byte swizzle row)
 constexpr int kStages = 4;          // TMA -> MMA pipeline depth
 constexpr int kMaxBN = 256;
 constexpr int kStageA = kBM * kBK * 2;        // 16 KiB
 constexpr int kStageB = kMaxBN * kBK * 2;     // 32 KiB
-constexpr int kTmemCols = 256;                // one 128 x 256 f32 accumulator
+constexpr int kAccCols = 256;                 // one 128 x 256 f32 accumulator
+constexpr int kTmemCols = 2 * kAccCols;       // double-buffered accumulators
+constexpr int kSlots = 2;                     // scheduler -> MMA / workers tile ring
 
 struct TileDesc {
   int32_t node;   // kernel id
@@ -74,9 +81,24 @@ struct Ctrl {
 
 enum DevErr : uint32_t { E_NONE = 0, E_DEP_TIMEOUT = 1, E_PIPE_TIMEOUT = 2, E_BAD_TILE = 3 };
 
+// Per-tile phase stamps (%globaltimer, ns), recorded when tracing is on.
+enum Stamp : int {
+  S_CLAIM = 0,     // scheduler claimed the queue position
+  S_READY = 1,     // scheduler: dependencies satisfied
+  S_LOADED = 2,    // scheduler: last TMA load of the tile issued (bf16 GEMM)
+  S_MMA0 = 3,      // MMA warp: accumulator free, first MMA issued
+  S_MMA1 = 4,      // MMA warp: last MMA issued and committed
+  S_WORK = 5,      // workers picked the tile up
+  S_ACC = 6,       // workers: accumulator complete observed (bf16 GEMM)
+  S_BODY = 7,      // workers: all output stores issued
+  S_SYNC = 8,      // workers: proxy fence + barrier done
+  S_END = 9,       // release done
+  kNumStamps = 10
+};
+
 struct TraceRec {
   uint32_t start_ticket, end_ticket, smid, tile;
-  uint64_t t_start, t_end;
+  uint64_t stamp[kNumStamps];
 };
 
 struct ExecParams {

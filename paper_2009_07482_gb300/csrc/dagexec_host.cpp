@@ -470,11 +470,14 @@ static void make_tiles(Plan &P) {
           for (int c = 0; c < N; c += bn)
             push(bf ? T_GEMM_BF16 : T_GEMM_F32, b * M + m, b * M + std::min(m + bm, M), c, std::min(c + bn, N), P.cfg[v]);
     } else if (n.op == DAG_OP_SOFTMAX) {
-      const int rows = C <= 1024 ? 128 : 32;
+      // 8 worker warps, two rows each in flight: 64-row tiles for short rows
+      const int rows = C <= 1024 ? 64 : 16;
       for (int r = 0; r < R; r += rows) push(T_SOFTMAX, r, std::min(r + rows, R), 0, C, 0);
     } else {
+      // about 32K elements per tile: enough tiles to spread a memory-bound
+      // kernel over many SMs, enough work per tile to amortise its claim
       int rows = 256;
-      while (rows > 8 && (long)rows * C > 131072) rows /= 2;
+      while (rows > 8 && (long)rows * C > 32768) rows /= 2;
       for (int r = 0; r < R; r += rows)
         push(n.op == DAG_OP_ADD ? T_ADD : T_UNARY, r, std::min(r + rows, R), 0, C, 0);
     }
@@ -1025,6 +1028,7 @@ extern "C" dag_status dag_submit(dag_handle *h, void *stream_) {
       return fail(DAG_EDEVICE, "cuStreamWriteValue32");
     }
   }
+  if (P.opt.trace && P.tiles.size()) CUDA_TRY(cudaMemsetAsync(h->d_trace, 0, P.tiles.size() * sizeof(TraceRec), stream));
   if (P.tiles.size()) CUDA_TRY(launch_persistent(h->xp, P.grid, stream));
   CUDA_TRY(cudaEventRecord(h->ev_done, stream));
   if ((s = enqueue_readbacks(h, stream))) return s;
@@ -1046,6 +1050,7 @@ extern "C" dag_status dag_submit_coarse(dag_handle *h, void *stream_) {
   }
   ExecParams x = h->xp;
   x.tiles = h->d_coarse;
+  if (P.opt.trace && P.tiles.size()) CUDA_TRY(cudaMemsetAsync(h->d_trace, 0, P.tiles.size() * sizeof(TraceRec), stream));
   for (int v : P.g.topo)
     if (P.node_count[v]) CUDA_TRY(launch_coarse(x, P.node_first[v], P.node_count[v], stream));
   CUDA_TRY(cudaEventRecord(h->ev_done, stream));
@@ -1111,6 +1116,11 @@ extern "C" dag_status dag_destroy(dag_handle *h) {
   return DAG_OK;
 }
 
+extern "C" dag_status dag_set_device(int ordinal) {
+  CUDA_TRY(cudaSetDevice(ordinal));
+  return DAG_OK;
+}
+
 extern "C" void *dag_host_alloc(size_t bytes) {
   void *p = nullptr;
   if (cudaHostAlloc(&p, bytes ? bytes : 1, cudaHostAllocDefault) != cudaSuccess) {
@@ -1137,8 +1147,21 @@ extern "C" dag_status dag_trace_get(dag_handle *h, dag_trace_record *out, int ca
   for (int i = 0; i < nt && i < cap; ++i) {
     const TileDesc &t = src[i];
     out[i] = dag_trace_record{t.node, t.r0, t.r1, t.c0, t.c1, tr[i].start_ticket, tr[i].end_ticket, tr[i].smid,
-                              tr[i].t_start, tr[i].t_end};
+                              tr[i].stamp[S_CLAIM], tr[i].stamp[S_READY], tr[i].stamp[S_WORK], tr[i].stamp[S_END]};
   }
+  return DAG_OK;
+}
+
+extern "C" dag_status dag_trace_stamps(dag_handle *h, uint64_t *out, int cap, int *n) {
+  if (!h || !n) return fail(DAG_EINVAL, "null argument");
+  if (h->in_flight) return fail(DAG_EBUSY, "call dag_wait first");
+  const int nt = (int)h->P.tiles.size();
+  *n = nt;
+  if (!out || cap <= 0) return DAG_OK;
+  if (!h->P.opt.trace) return fail(DAG_EINVAL, "tracing was not enabled in dag_options");
+  std::vector<TraceRec> tr(nt);
+  if (nt) CUDA_TRY(cudaMemcpy(tr.data(), h->d_trace, (size_t)nt * sizeof(TraceRec), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < nt && i < cap; ++i) memcpy(out + (size_t)i * kNumStamps, tr[i].stamp, sizeof tr[i].stamp);
   return DAG_OK;
 }
 

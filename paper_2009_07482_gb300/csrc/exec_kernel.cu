@@ -1,15 +1,25 @@
 // exec_kernel.cu -- the persistent DAG executor kernel (fine-grained path) and
 // its per-kernel launch form (coarse-grained baseline).
 //
-// Fine-grained mode: each CTA loops { claim the next queue position with one
-// atomic; wait (acquire, bounded) until the dependency counters of that tile
-// reach their targets; run the tile; release (increment) the counters of the
-// row blocks it wrote }.  The queue order is a linear extension of the tile
-// dependency graph, so any tile a CTA waits on was claimed earlier by a CTA
-// that is running and never waits on a later tile: the loop cannot deadlock
-// for any grid size, and the deadline bounds every wait regardless.  This
-// replaces the paper's host-side callback chain (Alg. 1: setup_cq, cb) with
-// device counters, at the granularity of output tiles rather than kernels.
+// Fine-grained mode: the CTAs pull output tiles of all kernels from one work
+// queue.  Inside a CTA three roles run concurrently, connected by mbarrier
+// rings in shared memory:
+//   scheduler (warp 0, lane 0): claim the next queue position with one
+//     atomic, wait (acquire, bounded) until the dependency counters of that
+//     tile reach their targets, publish it in the tile ring, and for a bf16
+//     GEMM tile stream its operands into the stage ring with TMA;
+//   MMA (warp 1, lane 0): for each bf16 GEMM tile, tcgen05.mma over the stage
+//     ring into one of two TMEM accumulators;
+//   workers (warps 4-11): GEMM epilogues (TMEM -> global) and every SIMT tile
+//     (f32 GEMM, softmax, elementwise); after a tile they release (increment)
+//     the counters of the row blocks it wrote.
+// So the next tile's dependency wait and operand loads overlap the current
+// tile's MMAs and epilogue.  The queue order is a linear extension of the
+// tile dependency graph and each CTA handles its tiles in claim order, so the
+// smallest unfinished queue position is always runnable: no deadlock for any
+// grid size, and every wait has a deadline regardless.  This replaces the
+// paper's host-side callback chain (Alg. 1: setup_cq, cb) with device
+// counters, at the granularity of output tiles rather than kernels.
 #include <climits>
 
 #include "dag_internal.h"
@@ -19,7 +29,19 @@
 namespace dagx {
 
 constexpr int kSmemStages = kStages * (kStageA + kStageB);
-constexpr int kSmemBytes = kSmemStages + 256 + 1024;  // stages + control block + alignment slack
+constexpr int kSmemCtl = (int)((sizeof(SmemCtl) + 255) / 256 * 256);
+constexpr int kSmemBytes = kSmemStages + kF32Smem + kSmemCtl + 1024;  // + alignment slack
+static_assert(kSmemBytes <= 232448, "shared memory budget");
+
+// worker-side broadcast values (written by the worker leader)
+struct WorkerShared {
+  int32_t tile;
+  int32_t ok;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 
 __device__ __forceinline__ void record_error(const ExecParams &p, uint32_t code, int tile) {
   if (atomicCAS(&p.ctrl->err_code, 0u, code) == 0u) p.ctrl->err_tile = (uint32_t)tile;
@@ -51,18 +73,205 @@ __device__ __forceinline__ bool wait_deps(const ExecParams &p, const TileDesc &t
   return true;
 }
 
+// ---------------------------------------------------------------------------
+// scheduler + TMA producer (one thread)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void run_scheduler(const ExecParams &p, uint8_t *smem, SmemCtl *ctl, uint32_t epoch) {
+  Ring slot = {0u, 0u}, st = {0u, 0u};
+  for (int iter = 0;; ++iter) {
+    int t = -1;
+    if (!ctl->fail) {
+      if (p.mode == 0) {
+        if (!ld_relaxed(&p.ctrl->abort)) {
+          t = (int)atomicAdd(&p.ctrl->head, 1u);
+          if (t >= p.n_tiles) t = -1;
+        }
+      } else if (iter == 0) {
+        t = p.tile_begin + (int)blockIdx.x;
+      }
+    }
+    TileDesc td;
+    uint64_t tc = 0, ts = 0;
+    uint32_t tk = 0;
+    if (t >= 0) {
+      td = p.tiles[t];
+      if (p.trace_on) tc = globaltimer();
+      if (p.trace_on) p.trace[t].stamp[S_CLAIM] = tc;
+      if (p.mode == 0) {
+        if (!wait_deps(p, td, epoch)) {
+          if (!ld_relaxed(&p.ctrl->abort)) record_error(p, E_DEP_TIMEOUT, t);
+          ctl->fail = 1;
+          t = -1;
+        } else {
+          fence_proxy_async_global();  // our TMA reads follow the acquired generic writes
+        }
+      }
+      if (t >= 0 && p.trace_on) {
+        tk = atomicAdd(&p.ctrl->ticket, 1u);
+        ts = globaltimer();
+        p.trace[t].stamp[S_READY] = ts;
+      }
+    }
+    // publish in the tile ring (the slot must have been consumed by MMA and workers)
+    if (!mbar_wait(&ctl->slot_empty[slot.idx], slot.phase ^ 1u, globaltimer() + 2 * p.timeout_ns + 1000000000ull)) {
+      record_error(p, E_PIPE_TIMEOUT, t);
+      ctl->fail = 1;
+      return;
+    }
+    TileSlot &s = ctl->slot[slot.idx];
+    s.t = t;
+    s.start_ticket = tk;
+    s.t_claim = tc;
+    s.t_start = ts;
+    mbar_arrive(&ctl->slot_full[slot.idx]);
+    slot.next(kSlots);
+    if (t < 0) return;
+    if (td.op == T_GEMM_BF16) {
+      if (!gemm_produce(p, td, p.nodes[td.node], smem, ctl, st, globaltimer() + p.timeout_ns)) {
+        record_error(p, E_PIPE_TIMEOUT, t);
+        ctl->fail = 1;
+      }
+      if (p.trace_on) p.trace[t].stamp[S_LOADED] = globaltimer();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// MMA issuer (one thread)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void run_mma(const ExecParams &p, uint8_t *smem, SmemCtl *ctl) {
+  Ring slot = {0u, 0u}, st = {0u, 0u};
+  uint32_t accb = 0, ph[2] = {0u, 0u};
+  const uint64_t slot_limit = 2 * p.timeout_ns + 1000000000ull;
+  for (;;) {
+    if (!mbar_wait(&ctl->slot_full[slot.idx], slot.phase, globaltimer() + slot_limit)) {
+      ctl->fail = 1;
+      return;
+    }
+    const int t = ctl->slot[slot.idx].t;
+    mbar_arrive(&ctl->slot_empty[slot.idx]);
+    slot.next(kSlots);
+    if (t < 0) return;
+    const TileDesc td = p.tiles[t];
+    if (td.op != T_GEMM_BF16) continue;
+    const uint64_t dl = globaltimer() + p.timeout_ns;
+    if (!mbar_wait(&ctl->acc_empty[accb], ph[accb] ^ 1u, dl)) { ctl->fail = 1; return; }
+    ph[accb] ^= 1u;
+    tc_fence_after();
+    if (p.trace_on) p.trace[t].stamp[S_MMA0] = globaltimer();
+    if (!gemm_mma(td, p.nodes[td.node], smem, ctl, st, ctl->tmem_base + accb * kAccCols, dl)) {
+      ctl->fail = 1;
+      return;
+    }
+    mma_commit(&ctl->acc_full[accb]);
+    if (p.trace_on) p.trace[t].stamp[S_MMA1] = globaltimer();
+    accb ^= 1u;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// workers (256 threads); every decision is taken by the leader and broadcast
+// through shared memory, so all workers reach the same named barriers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void run_workers(const ExecParams &p, uint8_t *smem, SmemCtl *ctl, WorkerShared *ws) {
+  const int wt = threadIdx.x - kWorkerBase;
+  Ring slot = {0u, 0u};
+  uint32_t accb = 0, ph[2] = {0u, 0u};
+  float *fsm = reinterpret_cast<float *>(smem + kSmemStages);
+  const uint64_t slot_limit = 2 * p.timeout_ns + 1000000000ull;
+  for (;;) {
+    if (wt == 0) {
+      const bool ok = mbar_wait(&ctl->slot_full[slot.idx], slot.phase, globaltimer() + slot_limit);
+      ws->tile = ok ? ctl->slot[slot.idx].t : -2;
+    }
+    worker_sync();
+    const int t = ws->tile;
+    if (t < 0) {
+      if (t == -2 && wt == 0) ctl->fail = 1;
+      return;
+    }
+    const TileSlot sl = ctl->slot[slot.idx];
+    const uint64_t t_work = (p.trace_on && wt == 0) ? globaltimer() : 0;
+    const TileDesc td = p.tiles[t];
+    const NodeParams &np = p.nodes[td.node];
+    bool ok = true;
+    switch (td.op) {
+      case T_GEMM_BF16: {
+        stage_bias(td, np, ctl);
+        if (wt == 0) {
+          ws->ok = mbar_wait(&ctl->acc_full[accb], ph[accb], globaltimer() + p.timeout_ns) ? 1 : 0;
+          if (p.trace_on) p.trace[t].stamp[S_ACC] = globaltimer();
+        }
+        worker_sync();
+        ph[accb] ^= 1u;
+        ok = ws->ok != 0;
+        if (ok) {
+          tc_fence_after();
+          gemm_epilogue(td, np, ctl, ctl->tmem_base + accb * kAccCols);
+        }
+        tc_fence_before();
+        break;
+      }
+      case T_GEMM_F32:
+        if (td.cfg == F32_128x128) tile_gemm_f32<128, 128>(td, np, fsm);
+        else if (td.cfg == F32_128x64) tile_gemm_f32<128, 64>(td, np, fsm);
+        else tile_gemm_f32<64, 64>(td, np, fsm);
+        break;
+      case T_ADD: tile_eltwise(td, np, true); break;
+      case T_UNARY: tile_eltwise(td, np, false); break;
+      case T_SOFTMAX: tile_softmax(td, np); break;
+      default: ok = false; break;
+    }
+    if (p.trace_on && wt == 0) p.trace[t].stamp[S_BODY] = globaltimer();
+    fence_proxy_async_global();  // this tile's generic stores, before any later TMA read of them
+    worker_sync();
+    if (wt == 0) {
+      if (p.trace_on) p.trace[t].stamp[S_SYNC] = globaltimer();
+      if (td.op == T_GEMM_BF16) mbar_arrive(&ctl->acc_empty[accb]);
+      if (!ok) {
+        record_error(p, td.op == T_GEMM_BF16 ? E_PIPE_TIMEOUT : E_BAD_TILE, t);
+        ctl->fail = 1;
+      } else {
+        __threadfence();
+        if (p.trace_on) {
+          TraceRec &r = p.trace[t];
+          r.start_ticket = sl.start_ticket;
+          r.end_ticket = atomicAdd(&p.ctrl->ticket, 1u);  // drawn before the release
+          r.smid = smid();
+          r.tile = (uint32_t)t;
+          r.stamp[S_WORK] = t_work;
+        }
+        if (p.mode == 0)
+          for (int i = 0; i < td.rel_count; ++i) red_release_add(&p.counters[p.rels[td.rel_begin + i]], 1u);
+        if (p.trace_on) p.trace[t].stamp[S_END] = globaltimer();
+      }
+      mbar_arrive(&ctl->slot_empty[slot.idx]);
+    }
+    if (td.op == T_GEMM_BF16) accb ^= 1u;
+    slot.next(kSlots);
+  }
+}
+
 __global__ void __launch_bounds__(kThreads, 1) dag_exec_kernel(const __grid_constant__ ExecParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  SmemCtl *ctl = reinterpret_cast<SmemCtl *>(smem + kSmemStages);
-  const int tid = threadIdx.x, warp = tid >> 5;
+  SmemCtl *ctl = reinterpret_cast<SmemCtl *>(smem + kSmemStages + kF32Smem);
+  __shared__ WorkerShared ws;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&ctl->full[s], 1);
       mbar_init(&ctl->empty[s], 1);
     }
-    mbar_init(&ctl->accum, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&ctl->acc_full[b], 1);
+      mbar_init(&ctl->acc_empty[b], 1);
+    }
+    for (int s = 0; s < kSlots; ++s) {
+      mbar_init(&ctl->slot_full[s], 1);
+      mbar_init(&ctl->slot_empty[s], 2);  // MMA warp + worker leader
+    }
     mbar_fence_init();
     ctl->fail = 0;
   }
@@ -74,75 +283,14 @@ __global__ void __launch_bounds__(kThreads, 1) dag_exec_kernel(const __grid_cons
   __syncthreads();
   tc_fence_after();
 
-  PipeState ps = {0u, 0u, 0u, 0u, 0u};
-  const uint32_t epoch = (p.mode == 0) ? ld_relaxed(&p.ctrl->epoch) : 0u;
-  int iter = 0;
-
-  for (;;) {
-    if (tid == 0) {
-      int t = INT_MAX;
-      if (p.mode == 0) {
-        if (!ld_relaxed(&p.ctrl->abort)) t = (int)atomicAdd(&p.ctrl->head, 1u);
-      } else if (iter == 0) {
-        t = p.tile_begin + (int)blockIdx.x;
-      }
-      if (t < p.n_tiles) {
-        if (p.mode == 0) {
-          if (!wait_deps(p, p.tiles[t], epoch)) {
-            if (!ld_relaxed(&p.ctrl->abort)) record_error(p, E_DEP_TIMEOUT, t);
-            t = INT_MAX;
-          }
-          fence_proxy_async_global();  // our TMA reads follow the acquired generic writes
-        }
-        if (t != INT_MAX && p.trace_on) {
-          ctl->start_ticket = atomicAdd(&p.ctrl->ticket, 1u);
-          ctl->t_start = globaltimer();
-        }
-      } else {
-        t = INT_MAX;
-      }
-      ctl->tile = t;
-    }
-    __syncthreads();
-    const int t = ctl->tile;
-    if (t >= p.n_tiles || ctl->fail) break;
-    ++iter;
-    const TileDesc td = p.tiles[t];
-    const NodeParams &np = p.nodes[td.node];
-    const uint64_t deadline = globaltimer() + p.timeout_ns;
-    switch (td.op) {
-      case T_GEMM_BF16:
-        if (!tile_gemm_bf16(p, td, np, smem, ctl, ps, deadline) && tid == 0) record_error(p, E_PIPE_TIMEOUT, t);
-        break;
-      case T_GEMM_F32:
-        if (td.cfg == F32_128x128) tile_gemm_f32<128, 128>(td, np, reinterpret_cast<float *>(smem));
-        else if (td.cfg == F32_128x64) tile_gemm_f32<128, 64>(td, np, reinterpret_cast<float *>(smem));
-        else tile_gemm_f32<64, 64>(td, np, reinterpret_cast<float *>(smem));
-        break;
-      case T_ADD: tile_eltwise(td, np, true); break;
-      case T_UNARY: tile_eltwise(td, np, false); break;
-      case T_SOFTMAX: tile_softmax(td, np); break;
-      default:
-        if (tid == 0) record_error(p, E_BAD_TILE, t);
-        break;
-    }
-    fence_proxy_async_global();  // make this tile's generic stores visible to later TMA readers
-    __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      if (p.trace_on) {
-        TraceRec r;
-        r.start_ticket = ctl->start_ticket;
-        r.end_ticket = atomicAdd(&p.ctrl->ticket, 1u);  // drawn before the release
-        r.smid = smid();
-        r.tile = (uint32_t)t;
-        r.t_start = ctl->t_start;
-        r.t_end = globaltimer();
-        p.trace[t] = r;
-      }
-      if (p.mode == 0)
-        for (int i = 0; i < td.rel_count; ++i) red_release_add(&p.counters[p.rels[td.rel_begin + i]], 1u);
-    }
+  if (warp == 0) {
+    if (lane == 0) run_scheduler(p, smem, ctl, p.mode == 0 ? ld_relaxed(&p.ctrl->epoch) : 0u);
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) run_mma(p, smem, ctl);
+    __syncwarp();
+  } else if (warp >= kWorkerBase / 32) {
+    run_workers(p, smem, ctl, &ws);
   }
 
   // teardown: free TMEM; the last CTA of a persistent launch rewinds the queue

@@ -1,8 +1,12 @@
-// tiles.cuh -- the tile kinds the executor runs.  Each function computes one
-// rectangle of one kernel's output with all 256 threads of the CTA.
+// tiles.cuh -- the tile kinds the executor runs.  GEMM main loops are split
+// between the producer and MMA warps; every other piece of work (GEMM
+// epilogues, f32 SIMT GEMMs, softmax, elementwise) runs on the 256 worker
+// threads, which synchronise among themselves with a named barrier.
 #pragma once
 #include <cuda_bf16.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 #include "dag_internal.h"
 #include "ptx.cuh"
@@ -35,168 +39,226 @@ __device__ __forceinline__ float activate(int act, float x) {
   return x;
 }
 
+// barrier among the 256 worker threads only (id 1; id 0 is __syncthreads)
+__device__ __forceinline__ void worker_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kWorkers) : "memory"); }
+
 // ---------------------------------------------------------------------------
 // Shared control block of one CTA (lives after the pipeline stages)
 // ---------------------------------------------------------------------------
-struct SmemCtl {
-  uint64_t full[kStages];   // TMA -> MMA: stage filled
-  uint64_t empty[kStages];  // MMA -> TMA: stage consumed
-  uint64_t accum;           // MMA -> epilogue: accumulator complete
-  uint32_t tmem_base;
-  int32_t tile;             // tile index broadcast by thread 0
-  int32_t fail;             // CTA-local failure flag
+struct TileSlot {
+  int32_t t;             // queue position, or -1 = no more tiles
   uint32_t start_ticket;
-  uint64_t t_start;
+  uint64_t t_claim, t_start;
 };
 
-// Pipeline phase state, persistent across tiles.  Thread 0 owns the producer
-// fields, thread 32 the MMA fields; every thread tracks the accumulator parity.
-struct PipeState {
-  uint32_t pstage, pphase, mstage, mphase, aphase;
+struct SmemCtl {
+  uint64_t full[kStages];      // TMA -> MMA: stage filled
+  uint64_t empty[kStages];     // MMA -> TMA: stage consumed
+  uint64_t acc_full[2];        // MMA -> workers: accumulator b complete
+  uint64_t acc_empty[2];       // workers -> MMA: accumulator b drained
+  uint64_t slot_full[kSlots];  // scheduler -> MMA, workers: slot published
+  uint64_t slot_empty[kSlots]; // MMA + workers -> scheduler: slot consumed
+  TileSlot slot[kSlots];
+  uint32_t tmem_base;
+  int32_t fail;                // CTA-local failure flag
+  float bias[kMaxBN];          // bias slice of the GEMM tile in the epilogue
+};
+
+// A position in a ring of mbarrier-guarded buffers.
+struct Ring {
+  uint32_t idx, phase;
+  __device__ __forceinline__ void next(uint32_t n) {
+    if (++idx == n) { idx = 0; phase ^= 1u; }
+  }
 };
 
 // ---------------------------------------------------------------------------
-// bf16 GEMM tile, 128 x BN, tcgen05 with the accumulator in TMEM
-//   thread 0  : TMA producer (A box 64x128, B boxes) into a kStages ring
-//   thread 32 : MMA issuer (4 x K=16 per stage), commits to the empty barriers
-//   all warps : epilogue, TMEM -> registers -> scale/bias/act/cast -> global
+// bf16 GEMM tile, 128 x BN on the tensor cores (tcgen05, f32 accumulator in
+// TMEM).  Producer side (scheduler warp, lane 0): all K blocks of the tile
+// into the stage ring.  A: box {64 (K), 128 (M)}; B K-major (trans_b):
+// box {64 (K), BN}; B MN-major: BN/64 boxes {64 (N), 64 (K)}.  All with the
+// 128-byte swizzle.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool tile_gemm_bf16(const ExecParams &p, const TileDesc &t, const NodeParams &np,
-                                               uint8_t *smem, SmemCtl *ctl, PipeState &ps,
-                                               uint64_t deadline) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int BN = t.cfg;
-  const int M = np.M, N = np.N;
-  const int bt = t.r0 / M;
-  const int m0 = t.r0 - bt * M;
-  const int n0 = t.c0;
+__device__ __forceinline__ bool gemm_produce(const ExecParams &p, const TileDesc &t, const NodeParams &np,
+                                             uint8_t *smem, SmemCtl *ctl, Ring &st, uint64_t deadline) {
+  const int BN = t.cfg, M = np.M;
+  const int bt = t.r0 / M, m0 = t.r0 - bt * M, n0 = t.c0;
   const int kiters = (np.K + kBK - 1) / kBK;
+  const CUtensorMap *ta = p.tmaps + np.tmap_a;
+  const CUtensorMap *tb = p.tmaps + np.tmap_b;
+  const int trans_b = np.trans_b;
+  const uint32_t bytes = (uint32_t)(kStageA + BN * kBK * 2);
   uint8_t *sA = smem;
   uint8_t *sB = smem + kStages * kStageA;
-  bool ok = true;
-
-  if (tid == 0) {
-    const CUtensorMap *ta = p.tmaps + np.tmap_a;
-    const CUtensorMap *tb = p.tmaps + np.tmap_b;
-    const uint32_t bytes = (uint32_t)(kStageA + BN * kBK * 2);
-    for (int kb = 0; kb < kiters; ++kb) {
-      if (!mbar_wait(&ctl->empty[ps.pstage], ps.pphase ^ 1u, deadline)) { ok = false; break; }
-      uint64_t *bar = &ctl->full[ps.pstage];
-      mbar_arrive_expect_tx(bar, bytes);
-      tma_load_3d(sA + ps.pstage * kStageA, ta, bar, kb * kBK, m0, bt);
-      uint8_t *dB = sB + ps.pstage * kStageB;
-      if (np.trans_b) {
-        tma_load_3d(dB, tb, bar, kb * kBK, n0, bt);                // box {64 (K), BN}
-      } else {
-        for (int j = 0; j < BN / 64; ++j)                          // boxes {64 (N), 64 (K)}
-          tma_load_3d(dB + j * (64 * kBK * 2), tb, bar, n0 + j * 64, kb * kBK, bt);
-      }
-      if (++ps.pstage == kStages) { ps.pstage = 0; ps.pphase ^= 1u; }
+  for (int kb = 0; kb < kiters; ++kb) {
+    if (!mbar_wait(&ctl->empty[st.idx], st.phase ^ 1u, deadline)) return false;
+    uint64_t *bar = &ctl->full[st.idx];
+    mbar_arrive_expect_tx(bar, bytes);
+    tma_load_3d(sA + st.idx * kStageA, ta, bar, kb * kBK, m0, bt);
+    uint8_t *dB = sB + st.idx * kStageB;
+    if (trans_b) {
+      tma_load_3d(dB, tb, bar, kb * kBK, n0, bt);
+    } else {
+      for (int j = 0; j < BN / 64; ++j) tma_load_3d(dB + j * (64 * kBK * 2), tb, bar, n0 + j * 64, kb * kBK, bt);
     }
-  } else if (tid == 32) {
-    const uint32_t idesc = idesc_bf16((uint32_t)BN, np.trans_b ? 0u : 1u);
-    const uint32_t tmem = ctl->tmem_base;
-    for (int kb = 0; kb < kiters; ++kb) {
-      if (!mbar_wait(&ctl->full[ps.mstage], ps.mphase, deadline)) { ok = false; break; }
-      tc_fence_after();
-      const uint32_t a0 = smem_u32(sA + ps.mstage * kStageA);
-      const uint32_t b0 = smem_u32(sB + ps.mstage * kStageB);
+    st.next(kStages);
+  }
+  return true;
+}
+
+// MMA side (MMA warp, lane 0): accumulate the tile into the TMEM columns at
+// tmem_d, then the caller commits to acc_full[b].
+__device__ __forceinline__ bool gemm_mma(const TileDesc &t, const NodeParams &np, uint8_t *smem, SmemCtl *ctl,
+                                         Ring &st, uint32_t tmem_d, uint64_t deadline) {
+  const int BN = t.cfg;
+  const int kiters = (np.K + kBK - 1) / kBK;
+  const int trans_b = np.trans_b;
+  const uint32_t idesc = idesc_bf16((uint32_t)BN, trans_b ? 0u : 1u);
+  uint8_t *sA = smem;
+  uint8_t *sB = smem + kStages * kStageA;
+  for (int kb = 0; kb < kiters; ++kb) {
+    if (!mbar_wait(&ctl->full[st.idx], st.phase, deadline)) return false;
+    tc_fence_after();
+    const uint32_t a0 = smem_u32(sA + st.idx * kStageA);
+    const uint32_t b0 = smem_u32(sB + st.idx * kStageB);
 #pragma unroll
-      for (int kk = 0; kk < kBK / 16; ++kk) {
-        // K-major, 128-byte swizzle: a K step of 16 bf16 is 32 bytes along the row
-        const uint64_t ad = smem_desc_sw128(a0 + kk * 32, 16, 1024);
-        // B K-major: same; B MN-major: 16 K rows of 128 bytes = 2048 bytes per step,
-        // 64-column chunks 8 KiB apart (leading offset), 8-row groups 1 KiB apart (stride offset)
-        const uint64_t bd = np.trans_b ? smem_desc_sw128(b0 + kk * 32, 16, 1024)
-                                       : smem_desc_sw128(b0 + kk * 2048, 64 * kBK * 2, 1024);
-        mma_bf16(tmem, ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
-      }
-      mma_commit(&ctl->empty[ps.mstage]);
-      if (++ps.mstage == kStages) { ps.mstage = 0; ps.mphase ^= 1u; }
+    for (int kk = 0; kk < kBK / 16; ++kk) {
+      // K-major, 128-byte swizzle: a K step of 16 bf16 is 32 bytes along the row.
+      // B MN-major: 16 K rows of 128 bytes = 2048 bytes per step, 64-column
+      // chunks 8 KiB apart (leading offset), 8-row groups 1 KiB apart (stride offset).
+      const uint64_t ad = smem_desc_sw128(a0 + kk * 32, 16, 1024);
+      const uint64_t bd = trans_b ? smem_desc_sw128(b0 + kk * 32, 16, 1024)
+                                  : smem_desc_sw128(b0 + kk * 2048, 64 * kBK * 2, 1024);
+      mma_bf16(tmem_d, ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
     }
-    if (ok) mma_commit(&ctl->accum);
+    mma_commit(&ctl->empty[st.idx]);
+    st.next(kStages);
   }
-  if (!ok) ctl->fail = 1;
+  return true;
+}
 
-  // ---- epilogue ----
-  const bool acc_ok = mbar_wait(&ctl->accum, ps.aphase, deadline);
-  ps.aphase ^= 1u;
-  if (!acc_ok) {
-    ctl->fail = 1;
-    return false;
-  }
-  tc_fence_after();
-  const int quad = warp & 3;            // TMEM lanes 32*quad .. 32*quad+31
-  const int half = warp >> 2;           // column half
+// Epilogue (workers): TMEM accumulator -> scale, bias, activation, cast ->
+// global.  Worker warp w reads TMEM lanes 32*(w%4).. and the columns of half
+// (w-4)/4 of the tile; each thread owns one output row.
+__device__ __forceinline__ void gemm_epilogue(const TileDesc &t, const NodeParams &npg, const SmemCtl *ctl,
+                                              uint32_t tmem_acc) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int BN = t.cfg;
+  const int M = npg.M, N = npg.N;
+  const int act = npg.act, c_dt = npg.c_dt, vec = npg.vec;
+  const float scale = npg.scale;
+  void *const Cp = npg.C;
+  const int64_t ldc = npg.ldc;
+  const int bt = t.r0 / M, m0 = t.r0 - bt * M, n0 = t.c0;
+  const int quad = warp & 3;
+  const int half = (warp - kWorkerBase / 32) >> 2;
   const int row = m0 + quad * 32 + lane;
   const bool row_ok = row < M;
   const int64_t grow = (int64_t)bt * M + row;
   const int cw = BN / 2;
-  const float scale = np.scale;
-  for (int c = half * cw; c < (half + 1) * cw; c += 16) {
-    float v[16];
-    tmem_ld16(ctl->tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)c, v);
+  for (int c = half * cw; c < (half + 1) * cw; c += 32) {
+    float v[32];
+    tmem_ld32(tmem_acc + ((uint32_t)(quad * 32) << 16) + (uint32_t)c, v);
     const int col = n0 + c;
-    if (!row_ok || col >= N) continue;
+    if (col >= N || !row_ok) continue;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      float x = v[i] * scale;
-      if (np.bias && col + i < N) x += load_elem(np.bias, np.bias_dt, col + i);
-      v[i] = activate(np.act, x);
-    }
-    if (np.vec && col + 16 <= N) {
-      if (np.c_dt == 1) {
-        uint32_t w[8];
+    for (int i = 0; i < 32; ++i) v[i] = activate(act, fmaf(v[i], scale, ctl->bias[c + i]));
+    if (vec && col + 32 <= N) {
+      if (c_dt == 1) {
+        uint4 *dst = reinterpret_cast<uint4 *>(static_cast<uint16_t *>(Cp) + grow * ldc + col);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) w[i] = (uint32_t)f32_to_bf16(v[2 * i]) | ((uint32_t)f32_to_bf16(v[2 * i + 1]) << 16);
-        uint4 *dst = reinterpret_cast<uint4 *>(static_cast<uint16_t *>(np.C) + grow * np.ldc + col);
-        dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
-        dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+        for (int q = 0; q < 4; ++q) {
+          uint32_t w[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            w[i] = (uint32_t)f32_to_bf16(v[8 * q + 2 * i]) | ((uint32_t)f32_to_bf16(v[8 * q + 2 * i + 1]) << 16);
+          dst[q] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
       } else {
-        float4 *dst = reinterpret_cast<float4 *>(static_cast<float *>(np.C) + grow * np.ldc + col);
+        float4 *dst = reinterpret_cast<float4 *>(static_cast<float *>(Cp) + grow * ldc + col);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+        for (int i = 0; i < 8; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
       }
     } else {
-      for (int i = 0; i < 16 && col + i < N; ++i) store_elem(np.C, np.c_dt, grow * np.ldc + col + i, v[i]);
+      for (int i = 0; i < 32 && col + i < N; ++i) store_elem(Cp, c_dt, grow * ldc + col + i, v[i]);
     }
   }
-  tc_fence_before();
-  return true;
+}
+
+// stage the bias slice [n0, n0+BN) of a GEMM tile in shared memory (workers)
+__device__ __forceinline__ void stage_bias(const TileDesc &t, const NodeParams &np, SmemCtl *ctl) {
+  const int wt = threadIdx.x - kWorkerBase;
+  const void *const bias = np.bias;
+  const int N = np.N, bdt = np.bias_dt;
+  for (int i = wt; i < t.cfg; i += kWorkers) {
+    const int n = t.c0 + i;
+    ctl->bias[i] = (bias && n < N) ? load_elem(bias, bdt, n) : 0.f;
+  }
 }
 
 // ---------------------------------------------------------------------------
-// f32 GEMM tile, exact f32 (SIMT FFMA), BM x BN with 16 x 16 threads, BK = 16,
-// double-buffered shared memory.  Each thread owns a (BM/16) x (BN/16) block
-// split into 4-wide groups 64 apart, so shared reads are conflict-free.
+// f32 GEMM tile, exact f32 (SIMT FFMA), BM x BN on the 256 workers as 16 x 16
+// threads, BK = 8, double-buffered shared memory.  Each thread owns a
+// (BM/16) x (BN/16) block split into 4-wide groups 64 apart, so shared reads
+// are conflict-free.
 // ---------------------------------------------------------------------------
+constexpr int kF32BK = 8;
+constexpr int kF32Smem = 2 * kF32BK * (128 + 4) * 4 * 2;  // bytes, for BM = BN = 128
+
 template <int BM, int BN>
-__device__ __forceinline__ void tile_gemm_f32(const TileDesc &t, const NodeParams &np, float *smem) {
-  constexpr int BK = 16;
+__device__ __forceinline__ void tile_gemm_f32(const TileDesc &t, const NodeParams &npg, float *smem) {
+  constexpr int BK = kF32BK;
   constexpr int TM = BM / 16, TN = BN / 16;
   constexpr int LDA_S = BM + 4, LDB_S = BN + 4;
   float *As = smem;                      // [2][BK][LDA_S]
   float *Bs = smem + 2 * BK * LDA_S;     // [2][BK][LDB_S]
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x - kWorkerBase;
   const int ty = tid >> 4, tx = tid & 15;
-  const int M = np.M, N = np.N, K = np.K;
+  const int M = npg.M, N = npg.N, K = npg.K;
+  const int trans_b = npg.trans_b, act = npg.act, c_dt = npg.c_dt, bias_dt = npg.bias_dt, vec = npg.vec;
+  const int64_t lda = npg.lda, ldb = npg.ldb, ldc = npg.ldc;
+  const float scale = npg.scale;
+  const void *const bias = npg.bias;
+  void *const Cp = npg.C;
   const int bt = t.r0 / M;
   const int m0 = t.r0 - bt * M, n0 = t.c0;
-  const float *A = static_cast<const float *>(np.A) + (int64_t)bt * M * np.lda;
-  const float *B = static_cast<const float *>(np.B) +
-                   (int64_t)bt * (np.trans_b ? (int64_t)N * np.ldb : (int64_t)K * np.ldb);
+  const float *A = static_cast<const float *>(npg.A) + (int64_t)bt * M * lda;
+  const float *B = static_cast<const float *>(npg.B) + (int64_t)bt * (trans_b ? (int64_t)N * ldb : (int64_t)K * ldb);
 
-  // loader mapping: A tile BM x BK -> EA elements per thread along k
-  constexpr int EA = BM * BK / kThreads;      // 4 or 8
-  constexpr int EB = BN * BK / kThreads;      // 4 or 8
+  // loader mapping: each thread moves EA (EB) consecutive elements of one row
+  constexpr int EA = BM * BK / kWorkers;      // 2 or 4
+  constexpr int EB = BN * BK / kWorkers;      // 2 or 4
   float ra[EA], rb[EB];
+
+  auto load_run = [&](float *dst, const float *src, int n, auto en_tag) {
+    constexpr int EN = decltype(en_tag)::value;
+    if constexpr (EN == 4) {
+      if (vec && n >= 4) {
+        const float4 v = __ldcg(reinterpret_cast<const float4 *>(src));
+        dst[0] = v.x; dst[1] = v.y; dst[2] = v.z; dst[3] = v.w;
+        return;
+      }
+    } else {
+      if (vec && n >= 2) {
+        const float2 v = __ldcg(reinterpret_cast<const float2 *>(src));
+        dst[0] = v.x; dst[1] = v.y;
+        return;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < EN; ++i) dst[i] = i < n ? __ldcg(src + i) : 0.f;
+  };
+  using TagA = std::integral_constant<int, EA>;
+  using TagB = std::integral_constant<int, EB>;
 
   auto load_a = [&](int k0) {
     const int r = tid / (BK / EA), kq = (tid % (BK / EA)) * EA;
     const int gm = m0 + r, gk = k0 + kq;
+    if (gm < M) load_run(ra, A + (int64_t)gm * lda + gk, K - gk, TagA{});
+    else {
 #pragma unroll
-    for (int i = 0; i < EA; ++i)
-      ra[i] = (gm < M && gk + i < K) ? __ldcg(A + (int64_t)gm * np.lda + gk + i) : 0.f;
+      for (int i = 0; i < EA; ++i) ra[i] = 0.f;
+    }
   };
   auto store_a = [&](int buf) {
     const int r = tid / (BK / EA), kq = (tid % (BK / EA)) * EA;
@@ -204,22 +266,26 @@ __device__ __forceinline__ void tile_gemm_f32(const TileDesc &t, const NodeParam
     for (int i = 0; i < EA; ++i) As[(buf * BK + kq + i) * LDA_S + r] = ra[i];
   };
   auto load_b = [&](int k0) {
-    if (np.trans_b) {  // B stored N x K
+    if (trans_b) {  // B stored N x K
       const int c = tid / (BK / EB), kq = (tid % (BK / EB)) * EB;
       const int gn = n0 + c, gk = k0 + kq;
+      if (gn < N) load_run(rb, B + (int64_t)gn * ldb + gk, K - gk, TagB{});
+      else {
 #pragma unroll
-      for (int i = 0; i < EB; ++i)
-        rb[i] = (gn < N && gk + i < K) ? __ldcg(B + (int64_t)gn * np.ldb + gk + i) : 0.f;
-    } else {           // B stored K x N
+        for (int i = 0; i < EB; ++i) rb[i] = 0.f;
+      }
+    } else {        // B stored K x N
       const int kr = tid / (BN / EB), cq = (tid % (BN / EB)) * EB;
       const int gk = k0 + kr, gn = n0 + cq;
+      if (gk < K) load_run(rb, B + (int64_t)gk * ldb + gn, N - gn, TagB{});
+      else {
 #pragma unroll
-      for (int i = 0; i < EB; ++i)
-        rb[i] = (gk < K && gn + i < N) ? __ldcg(B + (int64_t)gk * np.ldb + gn + i) : 0.f;
+        for (int i = 0; i < EB; ++i) rb[i] = 0.f;
+      }
     }
   };
   auto store_b = [&](int buf) {
-    if (np.trans_b) {
+    if (trans_b) {
       const int c = tid / (BK / EB), kq = (tid % (BK / EB)) * EB;
 #pragma unroll
       for (int i = 0; i < EB; ++i) Bs[(buf * BK + kq + i) * LDB_S + c] = rb[i];
@@ -241,7 +307,7 @@ __device__ __forceinline__ void tile_gemm_f32(const TileDesc &t, const NodeParam
   load_b(0);
   store_a(0);
   store_b(0);
-  __syncthreads();
+  worker_sync();
   for (int kt = 0; kt < nk; ++kt) {
     const int cur = kt & 1;
     if (kt + 1 < nk) {
@@ -270,11 +336,18 @@ __device__ __forceinline__ void tile_gemm_f32(const TileDesc &t, const NodeParam
       store_a(cur ^ 1);
       store_b(cur ^ 1);
     }
-    __syncthreads();
+    worker_sync();
   }
 
   // epilogue
-  const float scale = np.scale;
+  float bv[TN];
+#pragma unroll
+  for (int g = 0; g < TN / 4; ++g)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + g * 64 + tx * 4 + j;
+      bv[g * 4 + j] = (bias && n < N) ? load_elem(bias, bias_dt, n) : 0.f;
+    }
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
     const int m = m0 + (i / 4) * 64 + ty * 4 + (i % 4);
@@ -285,25 +358,20 @@ __device__ __forceinline__ void tile_gemm_f32(const TileDesc &t, const NodeParam
       const int n = n0 + g * 64 + tx * 4;
       float v[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        float x = acc[i][g * 4 + j] * scale;
-        if (np.bias && n + j < N) x += load_elem(np.bias, np.bias_dt, n + j);
-        v[j] = activate(np.act, x);
-      }
-      if (np.vec && n + 4 <= N && np.c_dt == 0) {
-        *reinterpret_cast<float4 *>(static_cast<float *>(np.C) + grow * np.ldc + n) =
-            make_float4(v[0], v[1], v[2], v[3]);
+      for (int j = 0; j < 4; ++j) v[j] = activate(act, fmaf(acc[i][g * 4 + j], scale, bv[g * 4 + j]));
+      if (vec && n + 4 <= N && c_dt == 0) {
+        *reinterpret_cast<float4 *>(static_cast<float *>(Cp) + grow * ldc + n) = make_float4(v[0], v[1], v[2], v[3]);
       } else {
-        for (int j = 0; j < 4 && n + j < N; ++j) store_elem(np.C, np.c_dt, grow * np.ldc + n + j, v[j]);
+        for (int j = 0; j < 4 && n + j < N; ++j) store_elem(Cp, c_dt, grow * ldc + n + j, v[j]);
       }
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-// Row softmax over whole rows [r0, r1): one warp per row, max and sum by warp
-// shuffles; rows of up to 1024 columns stay in registers (one read of the
-// input), longer rows are streamed three times.
+// Row softmax over whole rows [r0, r1): one warp per row, two rows per warp
+// in flight; max and sum by warp shuffles; rows of up to 32 * V columns stay
+// in registers (one read of the input), longer rows are streamed three times.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float warp_max(float v) {
 #pragma unroll
@@ -316,54 +384,81 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-__device__ __forceinline__ void tile_softmax(const TileDesc &t, const NodeParams &np) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+template <int V>
+__device__ __forceinline__ void softmax_rows_reg(const NodeParams &np, int r0, int r1, int stride) {
+  const int lane = threadIdx.x & 31;
   const int N = np.N;
   const float s = np.scale;
-  for (int r = t.r0 + warp; r < t.r1; r += kThreads / 32) {
-    const int64_t ia = (int64_t)r * np.lda, ic = (int64_t)r * np.ldc;
-    if (N <= 1024) {
-      float x[32];
+  const void *const A = np.A;
+  void *const C = np.C;
+  const int a_dt = np.a_dt, c_dt = np.c_dt;
+  const int64_t lda = np.lda, ldc = np.ldc;
+  for (int r = r0; r < r1; r += 2 * stride) {
+    const int rr[2] = {r, r + stride};
+    float x[2][V];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int i = 0; i < V; ++i) {
+        const int j = lane + 32 * i;
+        x[q][i] = (rr[q] < r1 && j < N) ? s * load_elem(A, a_dt, (int64_t)rr[q] * lda + j) : -INFINITY;
+      }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      if (rr[q] >= r1) continue;
       float m = -INFINITY;
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const int j = lane + 32 * i;
-        x[i] = j < N ? s * load_elem(np.A, np.a_dt, ia + j) : -INFINITY;
-        m = fmaxf(m, x[i]);
-      }
+      for (int i = 0; i < V; ++i) m = fmaxf(m, x[q][i]);
       m = warp_max(m);
       float sum = 0.f;
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const int j = lane + 32 * i;
-        x[i] = j < N ? expf(x[i] - m) : 0.f;
-        sum += x[i];
+      for (int i = 0; i < V; ++i) {
+        x[q][i] = (lane + 32 * i < N) ? expf(x[q][i] - m) : 0.f;
+        sum += x[q][i];
       }
       sum = warp_sum(sum);
       const float inv = 1.f / sum;
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
+      for (int i = 0; i < V; ++i) {
         const int j = lane + 32 * i;
-        if (j < N) store_elem(np.C, np.c_dt, ic + j, x[i] * inv);
+        if (j < N) store_elem(C, c_dt, (int64_t)rr[q] * ldc + j, x[q][i] * inv);
       }
-    } else {
+    }
+  }
+}
+
+__device__ __forceinline__ void tile_softmax(const TileDesc &t, const NodeParams &np) {
+  const int wid = (threadIdx.x - kWorkerBase) >> 5, lane = threadIdx.x & 31;
+  constexpr int nw = kWorkers / 32;
+  const int N = np.N;
+  if (N <= 256) {
+    softmax_rows_reg<8>(np, t.r0 + wid, t.r1, nw);
+  } else if (N <= 1024) {
+    softmax_rows_reg<32>(np, t.r0 + wid, t.r1, nw);
+  } else {
+    const float s = np.scale;
+    const void *const A = np.A;
+    void *const C = np.C;
+    const int a_dt = np.a_dt, c_dt = np.c_dt;
+    const int64_t lda = np.lda, ldc = np.ldc;
+    for (int r = t.r0 + wid; r < t.r1; r += nw) {
+      const int64_t ia = (int64_t)r * lda, ic = (int64_t)r * ldc;
       float m = -INFINITY;
-      for (int j = lane; j < N; j += 32) m = fmaxf(m, s * load_elem(np.A, np.a_dt, ia + j));
+      for (int j = lane; j < N; j += 32) m = fmaxf(m, s * load_elem(A, a_dt, ia + j));
       m = warp_max(m);
       float sum = 0.f;
-      for (int j = lane; j < N; j += 32) sum += expf(s * load_elem(np.A, np.a_dt, ia + j) - m);
+      for (int j = lane; j < N; j += 32) sum += expf(s * load_elem(A, a_dt, ia + j) - m);
       sum = warp_sum(sum);
       const float inv = 1.f / sum;
-      for (int j = lane; j < N; j += 32)
-        store_elem(np.C, np.c_dt, ic + j, expf(s * load_elem(np.A, np.a_dt, ia + j) - m) * inv);
+      for (int j = lane; j < N; j += 32) store_elem(C, c_dt, ic + j, expf(s * load_elem(A, a_dt, ia + j) - m) * inv);
     }
   }
 }
 
 // ---------------------------------------------------------------------------
 // Elementwise add / activation over rows [r0, r1) x cols [c0, c1): eight
-// consecutive elements per thread step, 128-bit loads and stores when the
-// rows are 16-byte aligned.
+// consecutive elements per step, 128-bit loads and stores when the rows are
+// 16-byte aligned, four steps per thread in flight.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void load8(const void *base, int dt, int64_t i, float (&v)[8]) {
   if (dt == 0) {
@@ -393,26 +488,53 @@ __device__ __forceinline__ void store8(void *base, int dt, int64_t i, const floa
   }
 }
 
-__device__ __forceinline__ void tile_eltwise(const TileDesc &t, const NodeParams &np, bool add) {
+__device__ __forceinline__ void tile_eltwise(const TileDesc &t, const NodeParams &npg, bool add) {
+  const void *const A = npg.A;
+  const void *const B = npg.B;
+  void *const C = npg.C;
+  const int64_t lda = npg.lda, ldb = npg.ldb, ldc = npg.ldc;
+  const int a_dt = npg.a_dt, b_dt = npg.b_dt, c_dt = npg.c_dt, act = npg.act, vec = npg.vec;
+  const int wt = threadIdx.x - kWorkerBase;
   const int width = t.c1 - t.c0;
-  const int groups = (width + 7) / 8;                // 8-element groups per row
-  const int64_t total = (int64_t)(t.r1 - t.r0) * groups;
-  for (int64_t g = threadIdx.x; g < total; g += kThreads) {
-    const int r = t.r0 + (int)(g / groups);
-    const int c = t.c0 + (int)(g % groups) * 8;
-    const int64_t ia = (int64_t)r * np.lda + c, ib = (int64_t)r * np.ldb + c, ic = (int64_t)r * np.ldc + c;
-    float a[8], b[8];
-    if (np.vec && c + 8 <= t.c1) {
-      load8(np.A, np.a_dt, ia, a);
-      if (add) load8(np.B, np.b_dt, ib, b);
+  const int groups = (width + 7) / 8;  // 8-element groups per row
+  const int total = (t.r1 - t.r0) * groups;
+  constexpr int U = 4;
+  for (int base = wt; base < total; base += U * kWorkers) {
+    float a[U][8], b[U][8];
+    int64_t ic[U];
+    int cc[U];
+    bool whole[U], live[U];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) a[k] = activate(np.act, add ? a[k] + b[k] : a[k]);
-      store8(np.C, np.c_dt, ic, a);
-    } else {
-      for (int k = 0; k < 8 && c + k < t.c1; ++k) {
-        float x = load_elem(np.A, np.a_dt, ia + k);
-        if (add) x += load_elem(np.B, np.b_dt, ib + k);
-        store_elem(np.C, np.c_dt, ic + k, activate(np.act, x));
+    for (int u = 0; u < U; ++u) {
+      const int g = base + u * kWorkers;
+      live[u] = g < total;
+      const int r = t.r0 + (live[u] ? g / groups : 0);
+      const int c = t.c0 + (live[u] ? (g % groups) * 8 : 0);
+      cc[u] = c;
+      whole[u] = live[u] && vec && c + 8 <= t.c1;
+      ic[u] = (int64_t)r * ldc + c;
+      const int64_t ia = (int64_t)r * lda + c, ib = (int64_t)r * ldb + c;
+      if (whole[u]) {
+        load8(A, a_dt, ia, a[u]);
+        if (add) load8(B, b_dt, ib, b[u]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          a[u][k] = (live[u] && c + k < t.c1) ? load_elem(A, a_dt, ia + k) : 0.f;
+          b[u][k] = (add && live[u] && c + k < t.c1) ? load_elem(B, b_dt, ib + k) : 0.f;
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!live[u]) continue;
+      float o[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) o[k] = activate(act, add ? a[u][k] + b[u][k] : a[u][k]);
+      if (whole[u]) {
+        store8(C, c_dt, ic[u], o);
+      } else {
+        for (int k = 0; k < 8 && cc[u] + k < t.c1; ++k) store_elem(C, c_dt, ic[u] + k, o[k]);
       }
     }
   }

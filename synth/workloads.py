@@ -85,11 +85,17 @@ class Workload:
     def output_ids(self) -> List[int]:
         return [i for i, b in enumerate(self.buffers) if b.role == "output"]
 
-    def make_inputs(self) -> Dict[int, np.ndarray]:
-        """Draw every input buffer and round it to its storage dtype."""
+    def make_inputs(self, cache: Optional[Dict] = None) -> Dict[int, np.ndarray]:
+        """Draw every input buffer and round it to its storage dtype.  `cache`
+        (a dict the caller keeps) reuses draws of equal recipe and shape."""
         out = {}
         for i in self.input_ids():
             b = self.buffers[i]
+            key = (b.init[0], b.init[1], b.init[2] if len(b.init) > 2 else None, b.rows, b.cols, b.dtype) \
+                if b.init[0] != "array" else None
+            if cache is not None and key in cache:
+                out[i] = cache[key]
+                continue
             kind = b.init[0]
             if kind == "uniform":
                 x = uniform(b.init[1], (b.rows, b.cols))
@@ -100,6 +106,8 @@ class Workload:
             else:
                 raise ValueError(kind)
             out[i] = to_storage(x, b.dtype)
+            if cache is not None and key is not None:
+                cache[key] = out[i]
         return out
 
     def clone(self) -> "Workload":
