@@ -200,6 +200,35 @@ dag_status dag_set_device(int ordinal);
 void *dag_host_alloc(size_t bytes);
 void dag_host_free(void *p);
 
+/*
+ * dag_run_noalloc: run a DAG on caller-owned device buffers without
+ * allocating any device memory.  The paper has no counterpart; this exists
+ * for callers that cannot call cudaMalloc (a process whose device memory is
+ * fully reserved by its own pool, code running inside an allocator or an
+ * error path, embedders whose allocator owns every device byte).
+ *   buffer_ptrs[i], row_pitch[i]: device address and row pitch (elements)
+ *     of every root buffer i (ignored for views, which live inside their
+ *     parent).  Pitches must be >= cols and a multiple of 16 bytes; pointers
+ *     16-byte aligned.  Inputs must already hold their data; outputs and
+ *     intermediates are written in place.
+ *   The executor's own working state (tile queue, dependency counters, node
+ *   parameters, TMA descriptors, control block) lives in a fixed 1 MiB device
+ *   array that every GPU loading this library holds until process exit.  A
+ *   DAG whose plan does not fit is rejected with DAG_ENOMEM before any device
+ *   work (roughly 15k tiles).
+ *   The call is synchronous: it enqueues on `stream`, waits for it, and
+ *   returns DAG_OK, DAG_ETIMEOUT (a device wait ran out) or an error.
+ *   The first call on each device looks up the array's device address with
+ *   that device current; make that first call before any stream capture.
+ *   Every call shares the one array and clears the parts that must start at
+ *   zero; calls that overlap on the GPU (from several host threads or
+ *   streams) race on it, so callers must serialise them.
+ *   opts may be NULL; tracing and the debug hook are ignored here.
+ */
+dag_status dag_run_noalloc(const dag_node_desc *nodes, int n_nodes, const dag_buffer_desc *buffers, int n_buffers,
+                           void *const *buffer_ptrs, const int64_t *row_pitch, const dag_options *opts,
+                           void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* Inspection                                                                */
 /* ------------------------------------------------------------------------ */

@@ -107,6 +107,8 @@ _SIGS = {
     "dag_set_peaks": (None, [C.c_double, C.c_double, C.c_double]),
     "dag_set_device": (i32, [C.c_int]),
     "dag_trace_stamps": (i32, [C.c_void_p, C.POINTER(u64), C.c_int, C.POINTER(C.c_int)]),
+    "dag_run_noalloc": (i32, [C.POINTER(dag_node_desc), C.c_int, C.POINTER(dag_buffer_desc), C.c_int,
+                              C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.POINTER(dag_options), C.c_void_p]),
 }
 
 
@@ -243,6 +245,18 @@ def dag_trace_stamps(h):
     out = (u64 * (10 * max(1, n.value)))()
     check(lib().dag_trace_stamps(h, out, n.value, C.byref(n)), "dag_trace_stamps")
     return np.frombuffer(out, dtype=np.uint64)[: 10 * n.value].reshape(-1, 10).copy()
+
+
+def dag_run_noalloc(nodes, buffers, buffer_ptrs, row_pitch, options: Optional[dag_options] = None,
+                    stream: int = 0) -> int:
+    """Run a DAG on caller-owned device buffers with no device allocation
+    (synchronous); returns the status so callers can test DAG_ENOMEM etc."""
+    na, nn = _arr(dag_node_desc, nodes)
+    ba, nb = _arr(dag_buffer_desc, buffers)
+    pa = (C.c_void_p * max(1, nb))(*[C.c_void_p(p) for p in buffer_ptrs])
+    la = (C.c_int64 * max(1, nb))(*row_pitch)
+    return int(lib().dag_run_noalloc(na, nn, ba, nb, pa, la, C.byref(options) if options else None,
+                                     C.c_void_p(stream)))
 
 
 def dag_plan_get(h) -> dag_plan_info:

@@ -5,6 +5,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
+#include "dagexec.h"
+
 namespace dagx {
 
 // Tile kinds.  A tile is a rectangle of one kernel's output buffer.
@@ -124,5 +128,16 @@ cudaError_t exec_prepare();  // sets the kernel's shared-memory attribute (once 
 cudaError_t launch_persistent(const ExecParams &p, int grid, cudaStream_t s);
 cudaError_t launch_coarse(const ExecParams &p, int tile_begin, int n, cudaStream_t s);
 int max_coresident_ctas_per_sm();
+
+// Plan a DAG over caller-owned device buffers and serialise every device-side
+// plan array (tensor maps, queue, waits, releases, node parameters, zeroed
+// counters, flags and control block) into `blob`, laid out for a device
+// region starting at `region` of `capacity` bytes; fills the kernel
+// parameters that point into that region.  DAG_ENOMEM if it does not fit.
+dag_status plan_into_region(const dag_node_desc *nodes, int n_nodes, const dag_buffer_desc *buffers, int n_buffers,
+                            void *const *ptrs, const int64_t *lds, const dag_options *opts, char *region,
+                            size_t capacity, std::vector<char> &blob, ExecParams &xp, int &grid);
+// set the thread-local message returned by dag_last_error
+dag_status report_error(dag_status s, const char *msg);
 
 }  // namespace dagx

@@ -1190,3 +1190,122 @@ extern "C" dag_status dag_tiles_get(dag_handle *h, int32_t *out6, int cap, int *
   }
   return DAG_OK;
 }
+
+// ---------------------------------------------------------------------------
+// A whole plan serialised into one caller-provided device region.  Used by
+// the entry point that allocates nothing (noalloc.cu): the region is a
+// file-scope device array there, the buffers belong to the caller.
+// ---------------------------------------------------------------------------
+dag_status dagx::report_error(dag_status s, const char *msg) { return fail(s, "%s", msg); }
+
+dag_status dagx::plan_into_region(const dag_node_desc *nodes, int n_nodes, const dag_buffer_desc *buffers,
+                                  int n_buffers, void *const *ptrs, const int64_t *lds, const dag_options *opts,
+                                  char *region, size_t capacity, std::vector<char> &blob, ExecParams &xp,
+                                  int &grid) {
+  dag_status s = init_driver();
+  if (s) return s;
+  if (n_buffers > 0 && (!ptrs || !lds)) return fail(DAG_EINVAL, "null buffer pointer or pitch array");
+  Plan P;
+  if (opts) P.opt = *opts;
+  if (!P.opt.timeout_ns) P.opt.timeout_ns = 2000000000ull;
+  P.opt.trace = 0;
+  P.opt.debug_never_ready = 0;
+  // every input is already in the caller's device memory: no upload flags
+  std::vector<dag_buffer_desc> bufs(buffers, buffers + std::max(0, n_buffers));
+  for (auto &b : bufs)
+    if (b.flags & DAG_BUF_INPUT) b.flags |= DAG_BUF_RESIDENT;
+  if ((s = build_graph(nodes, n_nodes, nullptr, 0, bufs.data(), n_buffers, P.g))) return s;
+  Graph &g = P.g;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(DAG_EDEVICE, "no CUDA device");
+  cudaDeviceGetAttribute(&P.n_sm, cudaDevAttrMultiProcessorCount, dev);
+  P.grid = P.n_sm * std::max(1, max_coresident_ctas_per_sm());
+  if (P.opt.max_ctas > 0) P.grid = std::min(P.grid, P.opt.max_ctas);
+  plan_tiles(P);
+  grid = P.grid;
+
+  // caller buffers: root pointer and pitch; views offset into their parent
+  std::vector<char *> dptr(g.nb, nullptr);
+  std::vector<int64_t> ld(g.nb, 0);
+  for (int b = 0; b < g.nb; ++b) {
+    const int r = g.root[b];
+    if (!ptrs[r]) return fail(DAG_EINVAL, "buffer %d: null device pointer", r);
+    if (lds[r] < g.bufs[r].cols || (lds[r] * esize(g.bufs[r].dtype)) % 16)
+      return fail(DAG_EUNSUPPORTED, "buffer %d: row pitch %lld must be >= cols and a multiple of 16 bytes", r,
+                  (long long)lds[r]);
+    if ((uintptr_t)ptrs[r] % 16) return fail(DAG_EUNSUPPORTED, "buffer %d: pointer not 16-byte aligned", r);
+    ld[b] = lds[r];
+    dptr[b] = (char *)ptrs[r] + (size_t)g.coff[b] * esize(g.bufs[b].dtype);
+  }
+  const int nn = g.nn, nt = (int)P.queue.size();
+  std::vector<NodeParams> np(std::max(1, nn));
+  std::vector<CUtensorMap> maps;
+  for (int v = 0; v < nn; ++v) {
+    const dag_node_desc &n = g.nodes[v];
+    NodeParams &q = np[v];
+    memset(&q, 0, sizeof q);
+    q.A = dptr[n.a];
+    q.lda = ld[n.a];
+    q.a_dt = g.bufs[n.a].dtype;
+    if (n.op == DAG_OP_GEMM || n.op == DAG_OP_ADD) { q.B = dptr[n.b]; q.ldb = ld[n.b]; q.b_dt = g.bufs[n.b].dtype; }
+    if (n.op == DAG_OP_GEMM && n.bias >= 0) { q.bias = dptr[n.bias]; q.bias_dt = g.bufs[n.bias].dtype; }
+    q.C = dptr[n.out];
+    q.ldc = ld[n.out];
+    q.c_dt = g.bufs[n.out].dtype;
+    q.M = g.M[v]; q.N = g.N[v]; q.K = g.K[v]; q.batch = n.op == DAG_OP_GEMM ? n.batch : 1;
+    q.trans_b = n.trans_b; q.act = n.act; q.scale = n.scale;
+    q.tmap_a = q.tmap_b = -1;
+    bool vec = true;
+    int in[3];
+    const int k = g.inputs(v, in);
+    for (int i = 0; i < k; ++i) vec &= ((uintptr_t)dptr[in[i]] % 16) == 0;
+    vec &= ((uintptr_t)dptr[n.out] % 16) == 0;
+    q.vec = vec ? 1 : 0;
+    if (n.op == DAG_OP_GEMM && q.a_dt == DAG_BF16) {
+      if (((uintptr_t)q.A % 16) || ((uintptr_t)q.B % 16))
+        return fail(DAG_EUNSUPPORTED, "node %d: bf16 GEMM operand view not 16-byte aligned", v);
+      const int M = q.M, N = q.N, K = q.K, B = n.batch;
+      CUtensorMap ma, mb;
+      if ((s = encode_map(&ma, q.A, K, M, B, q.lda * 2, (uint64_t)M * q.lda * 2, kBK, kBM))) return s;
+      if (n.trans_b) s = encode_map(&mb, q.B, K, N, B, q.ldb * 2, (uint64_t)N * q.ldb * 2, kBK, P.cfg[v]);
+      else s = encode_map(&mb, q.B, N, K, B, q.ldb * 2, (uint64_t)K * q.ldb * 2, 64, kBK);
+      if (s) return s;
+      q.tmap_a = (int)maps.size(); maps.push_back(ma);
+      q.tmap_b = (int)maps.size(); maps.push_back(mb);
+    }
+  }
+  // layout inside the region; counters, flags and control block start at zero
+  size_t o_maps = 0;
+  size_t o_tiles = align_up(o_maps + maps.size() * sizeof(CUtensorMap), 256);
+  size_t o_waits = align_up(o_tiles + (size_t)nt * sizeof(TileDesc), 256);
+  size_t o_rels = align_up(o_waits + P.waits.size() * sizeof(Wait), 256);
+  size_t o_nodes = align_up(o_rels + P.rels.size() * sizeof(uint32_t), 256);
+  size_t o_cnt = align_up(o_nodes + np.size() * sizeof(NodeParams), 256);
+  size_t o_flags = align_up(o_cnt + (size_t)std::max(1, P.n_counters) * 4, 256);
+  size_t o_ctrl = align_up(o_flags + (size_t)std::max(1, P.n_flags) * 4, 256);
+  size_t total = align_up(o_ctrl + sizeof(Ctrl), 256);
+  if (total > capacity)
+    return fail(DAG_ENOMEM, "this DAG's plan needs %zu bytes of scratch (%d tiles); the fixed scratch holds %zu bytes",
+                total, nt, capacity);
+  blob.assign(total, 0);
+  auto put = [&](size_t o, const void *src, size_t n) { if (n) memcpy(blob.data() + o, src, n); };
+  put(o_maps, maps.data(), maps.size() * sizeof(CUtensorMap));
+  put(o_tiles, P.queue.data(), (size_t)nt * sizeof(TileDesc));
+  put(o_waits, P.waits.data(), P.waits.size() * sizeof(Wait));
+  put(o_rels, P.rels.data(), P.rels.size() * sizeof(uint32_t));
+  put(o_nodes, np.data(), np.size() * sizeof(NodeParams));
+  memset(&xp, 0, sizeof xp);
+  xp.tiles = (const TileDesc *)(region + o_tiles);
+  xp.n_tiles = nt;
+  xp.waits = (const Wait *)(region + o_waits);
+  xp.rels = (const uint32_t *)(region + o_rels);
+  xp.nodes = (const NodeParams *)(region + o_nodes);
+  xp.tmaps = (const CUtensorMap *)(region + o_maps);
+  xp.counters = (uint32_t *)(region + o_cnt);
+  xp.flags = (uint32_t *)(region + o_flags);
+  xp.ctrl = (Ctrl *)(region + o_ctrl);
+  xp.trace = nullptr;
+  xp.trace_on = 0;
+  xp.timeout_ns = P.opt.timeout_ns;
+  return DAG_OK;
+}
