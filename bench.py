@@ -43,14 +43,19 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mlp_bf16",
-                    choices=["mlp_bf16", "mlp_f32", "fork_join", "encoder"])
+                    choices=["mlp_bf16", "mlp_f32", "fork_join", "encoder", "batched"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="few steps, no side measurements (for ncu)")
     return ap.parse_args()
 
 
 def make_workload(name):
-    from synth.workloads import branchy_mlp, encoder_block, fork_join
+    """(workload, description); for "batched" the workload is the list of DAGs."""
+    from synth.workloads import branchy_mlp, encoder_block, fork_join, random_batch
+    if name == "batched":
+        return random_batch(256), ("256 seeded random layered DAGs (8-64 nodes, widths 1-8; GEMM 70% / eltwise 20% / "
+                                   "softmax 10%; M,N,K in {64..2048}; bf16 or f32 per DAG) in one persistent launch "
+                                   "replayed from a CUDA graph")
     if name == "mlp_bf16":
         return branchy_mlp("bf16"), ("branchy MLP inference DAG, bf16 in / f32 accumulate: batch 512, 4 branches x 3 "
                                      "Linear(2048,2048)+bias+ReLU, add tree, Linear(2048,4096)+ReLU, Linear(4096,1024)")
@@ -113,6 +118,16 @@ def oracle_model(workload, ra=4, rb=12):
         w = fork_join(256)
         t = _oracle_seconds(w, w.make_inputs(), repeat=3)
         return t, "fork-join 256^3 f32: the whole DAG, mean of 3 runs", (w, 256, t, 0.0)
+    if workload == "batched":
+        from synth.workloads import random_batch
+        ws = random_batch(256)
+        flops = [sum(x.node_flops(k) for k, n in enumerate(x.nodes) if n.op == "gemm") for x in ws]
+        # the three DAGs with the least GEMM work, whole, scaled by total work
+        pick = sorted(range(len(ws)), key=lambda i: flops[i])[:3]
+        t = sum(_oracle_seconds(ws[i], ws[i].make_inputs(_INPUTS)) for i in pick)
+        scale = sum(flops) / max(1.0, sum(flops[i] for i in pick))
+        return (t * scale, f"random batch: DAGs {pick} whole ({t:.2f} s), scaled by total GEMM flops (x{scale:.0f})",
+                (None, 0, t, 0.0))
     w = encoder_block(batch=1)
     t = _oracle_seconds(w, w.make_inputs())
     return 8 * t, f"encoder block: 1 of 8 independent sequences (all 99 kernels, {t:.2f} s), times 8", (w, 1, t, 0.0)
@@ -120,7 +135,8 @@ def oracle_model(workload, ra=4, rb=12):
 
 def oracle_sample(workload):
     full, desc, _ = oracle_model(workload)
-    return {"value": 1.0 / full, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+    n_dags = 256 if workload == "batched" else 1
+    return {"value": n_dags / full, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
 
 
 def run_reference(args):
@@ -136,6 +152,18 @@ def run_reference(args):
         from synth.workloads import branchy_mlp
         rows = 1
         w = branchy_mlp("bf16" if args.workload == "mlp_bf16" else "f32", batch=rows)
+    if w is None:  # batched: the calibration run is the step
+        per = [full] * args.steps
+        ms = full * 1e3
+        line = {"impl": "reference", "metric": METRIC, "value": 1e3 / ms * 256, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+                "config": {"workload": desc, "parallelism": "host oracle, rank 0 only"},
+                "cpu_baseline": {"value": 1e3 / ms * 256, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": cal_desc},
+                "e2e": {"value": 1e3 / ms * 256, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
     ins = w.make_inputs(_INPUTS)
     scale_rows = 512 if args.workload.startswith("mlp") else None
     per = []
@@ -258,12 +286,31 @@ def main():
     peaks, peaks_src = load_peaks()
     abi.dag_set_peaks(peaks["bf16_tflops"], 0.0, peaks["hbm_gbs"])
 
-    w, desc = make_workload(args.workload)
-    ins = w.make_inputs(_INPUTS)
-    X = w.input_ids()[0]
-    Y = w.output_ids()[0]
+    wl, desc = make_workload(args.workload)
+    batched = isinstance(wl, list)
+    from synth.workloads import concat
+    w = concat(wl) if batched else wl
+    n_dags = len(wl) if batched else 1
+    if batched:
+        ins, off = {}, 0
+        for x in wl:
+            ins.update({off + i: a for i, a in x.make_inputs(_INPUTS).items()})
+            off += len(x.buffers)
+    else:
+        ins = w.make_inputs(_INPUTS)
+    # per-step inputs: the activations (inputs not used as GEMM weights or biases)
+    weights = {n.b for n in w.nodes if n.op == "gemm"} | {n.bias for n in w.nodes if n.op == "gemm" and n.bias >= 0}
+    X_ids = [i for i in w.input_ids() if i not in weights]
+    Y_ids = w.output_ids()
+
+    def make_dag(streamed):
+        o = options(use_graph=1 if batched else 0)
+        if batched:
+            return Dag.batch(wl, o, resident_inputs=not streamed, streamed=set(X_ids) if streamed else None)
+        return Dag(w, o, streamed=set(X_ids)) if streamed else Dag(w, o, resident_inputs=True)
+
     # device-resident run: every input resident
-    d = Dag(w, options(), resident_inputs=True)
+    d = make_dag(False)
     d.set_inputs(ins)
     d.run()
     info = d.plan()
@@ -301,7 +348,7 @@ def main():
         print(json.dumps({"profile_run": True, "median_us": statistics.median(fine_us)}))
         d.close()
         return 0
-    coarse_us, _ = timed(d.submit_coarse, max(10, args.steps // 4), 3)
+    coarse_us, _ = timed(d.submit_coarse, max(3, args.steps // 4) if batched else max(10, args.steps // 4), 3)
     n_coarse_launches = sum(1 for _ in w.nodes)
 
     # max over ranks of the mean step time
@@ -310,48 +357,63 @@ def main():
         t = torch.tensor([mean_us], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         mean_us = float(t.item())
-    value = world * 1e6 / mean_us
+    value = world * n_dags * 1e6 / mean_us
     med = statistics.median(fine_us)
     q = np.percentile(fine_us, [10, 90])
     cmed = statistics.median(coarse_us)
 
-    # e2e: host buffers through the C ABI (X streamed from pinned memory, Y read back)
+    # e2e: host buffers through the C ABI (activations streamed from pinned
+    # memory every step, every sink read back into pinned memory)
     d.close()
-    e = Dag(w, options(), streamed={X})
-    e.set_inputs({k: v for k, v in ins.items() if k != X})
+    e = make_dag(True)
+    e.set_inputs({k: v for k, v in ins.items() if k not in X_ids})
     e.run()
-    e.set_inputs({X: ins[X]}, pinned=True)
-    ybytes = w.buffers[Y].rows * w.buffers[Y].cols * (4 if w.buffers[Y].dtype == "f32" else 2)
-    ypin = abi.dag_host_alloc(ybytes)
-    abi.dag_set_output(e.h, Y, ypin)
+    e.set_inputs({k: ins[k] for k in X_ids}, pinned=True)
+    pins = []
+    ybytes = 0
+    for Y in Y_ids:
+        nb = w.buffers[Y].rows * w.buffers[Y].cols * (4 if w.buffers[Y].dtype == "f32" else 2)
+        pins.append(abi.dag_host_alloc(nb))
+        abi.dag_set_output(e.h, Y, pins[-1])
+        ybytes += nb
     for _ in range(max(3, args.warmup)):
         e.submit(sp)
         abi.check(e.wait(), "wait")
     barrier()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    e2e_steps = args.steps if not batched else max(3, args.steps // 4)
+    for _ in range(e2e_steps):
         e.submit(sp)
         abi.check(e.wait(), "wait")
     barrier()
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    xbytes = ins[X].nbytes
-    abi.dag_set_output(e.h, Y, None)
-    abi.dag_host_free(ypin)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    xbytes = sum(ins[k].nbytes for k in X_ids)
+    for Y in Y_ids:
+        abi.dag_set_output(e.h, Y, None)
+    for pnt in pins:
+        abi.dag_host_free(pnt)
     e.close()
 
     # roofline of the executor kernel (the only kernel of a step)
-    bf16 = "bf16" in args.workload or args.workload == "encoder"
-    if bf16:
-        peak = peaks["bf16_tflops"]
-        achieved = info.flops / (mean_us * 1e-6) / 1e12
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": f"{peaks_src} bf16 burst (MEASURED_PEAKS.json)" if peaks_src == "measured" else "fallback"}
+    # f32 GEMMs run on the FP32 ALUs: 152 SMs x 128 FFMA/clk x 2 flop x max SM clock
+    f32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    fl = {"bf16": 0.0, "f32": 0.0}
+    for k, n in enumerate(w.nodes):
+        if n.op == "gemm":
+            fl[w.buffers[n.a].dtype] += w.node_flops(k)
+    t_bound_us = (fl["bf16"] / peaks["bf16_tflops"] + fl["f32"] / f32_peak) / 1e6
+    achieved = info.flops / (mean_us * 1e-6) / 1e12
+    src_bf16 = f"{peaks_src} bf16 burst (MEASURED_PEAKS.json)" if peaks_src == "measured" else "fallback 1.9 PF/s"
+    src_f32 = "derived: 152 SMs x 128 f32 FMA/clk x 2 flop x max SM clock"
+    if fl["f32"] == 0:
+        roof = {"bound": "tensor", "peak": peaks["bf16_tflops"], "peak_source": src_bf16}
+    elif fl["bf16"] == 0:
+        roof = {"bound": "alu", "peak": f32_peak, "peak_source": src_f32}
     else:
-        # f32 GEMMs on the FP32 ALUs: peak = 152 SMs x 128 FFMA/clk x 2 x max clock
-        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        achieved = info.flops / (mean_us * 1e-6) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": "derived: 152 SMs x 128 f32 FMA/clk x 2 flop x max SM clock"}
+        roof = {"bound": "tensor", "peak": info.flops / t_bound_us / 1e6,
+                "peak_source": f"flop-weighted: bf16 at {src_bf16}, f32 at {src_f32}"}
+    roof.update({"achieved": achieved, "unit": "TFLOP/s", "frac": achieved / roof["peak"]})
+    bf16 = fl["bf16"] > 0 and fl["f32"] == 0
     traffic, sha = traffic_for(args.workload)
     roof["traffic"] = traffic
     roof["algorithmic"] = {"flops_per_launch": info.flops, "bytes_per_launch": info.bytes}
@@ -361,8 +423,10 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mean_us / 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16" if bf16 else "f32", "data": "synthetic (seeded SplitMix64)",
-        "config": {"workload": desc, "nodes": len(w.nodes), "tiles": info.n_tiles, "grid": info.grid,
+        "vs_baseline": None, "dtype": "bf16" if bf16 else ("f32" if fl["bf16"] == 0 else "bf16+f32"),
+        "data": "synthetic (seeded SplitMix64)",
+        "config": {"workload": desc, "dags_per_step": n_dags, "nodes": len(w.nodes), "tiles": info.n_tiles,
+                   "grid": info.grid,
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": f"replicas x{world} (independent DAGs per GPU)" if world > 1 else "1 GPU"},
         "makespan_us": {"median": med, "p10": float(q[0]), "p90": float(q[1]), "mean": statistics.mean(fine_us)},
@@ -371,7 +435,7 @@ def main():
         "cp_roofline": {"critical_path_us": info.critical_path_us, "work_bound_us": info.work_bound_us,
                         "frac_of_cp": info.critical_path_us / med, "frac_of_work_bound": info.work_bound_us / med},
         "roofline": roof,
-        "e2e": {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(xbytes),
+        "e2e": {"value": world * n_dags / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(xbytes),
                 "d2h_bytes_per_step": int(ybytes), "ms_per_step": e2e_s * 1e3},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),

@@ -127,7 +127,10 @@ typedef struct {
   const float *node_cost_us;  /* per-node time estimates for DAG_SCHED_RANK_GIVEN (n_nodes entries) */
   int32_t debug_never_ready;  /* test hook: >0 makes that many tiles wait on a counter nothing releases,
                                  so the device wait runs out and reports DAG_ETIMEOUT */
-  int32_t reserved[7];
+  int32_t use_graph;          /* 1: dag_submit replays the persistent launch from a captured CUDA graph */
+  int32_t autotune;           /* 1: dag_create times candidate plans (tile widths x queue orders) on the
+                                 device with zeroed buffers and keeps the fastest (see dag_plan_info) */
+  int32_t reserved[5];
 } dag_options;
 
 typedef struct dag_handle dag_handle;
@@ -142,6 +145,23 @@ typedef struct dag_handle dag_handle;
 dag_status dag_create(const dag_node_desc *nodes, int n_nodes, const dag_edge *edges, int n_edges,
                       const dag_buffer_desc *buffers, int n_buffers, const dag_options *opts,
                       dag_handle **out);
+
+/*
+ * dag_batch_create: many DAGs in one plan and one persistent launch (a batch
+ * is a DAG whose connected components are the items; their tiles share one
+ * work queue, so small and large DAGs fill the GPU together).  Buffer ids of
+ * item i in the returned handle are offset by the buffer counts of items
+ * 0..i-1; node ids likewise by their node counts.  Everything else is as for
+ * dag_create (opts applies to the whole batch).
+ */
+typedef struct {
+  const dag_node_desc *nodes;
+  int32_t n_nodes;
+  const dag_buffer_desc *buffers;
+  int32_t n_buffers;
+} dag_batch_item;
+
+dag_status dag_batch_create(const dag_batch_item *items, int n_items, const dag_options *opts, dag_handle **out);
 
 /*
  * dag_set_input: give the host data of input buffer `buf` (rows x cols,
@@ -293,6 +313,8 @@ typedef struct {
   double flops, bytes;           /* algorithmic totals (2MNK per GEMM; each operand read once + output written once) */
   double critical_path_us;       /* sum over the critical path of max(flops/peak, bytes/bw) under the peaks given to dag_set_peaks */
   double work_bound_us;          /* max(critical path, total flops/peak, total bytes/bw) */
+  int32_t tile_override, scheduler;  /* the plan's tile policy and queue order (the autotuner's choice) */
+  double tuned_us;               /* autotune: measured makespan of the chosen plan (0 if not tuned) */
 } dag_plan_info;
 
 dag_status dag_plan_get(dag_handle *h, dag_plan_info *out);

@@ -45,7 +45,7 @@ class dag_edge(C.Structure):
 class dag_options(C.Structure):
     _fields_ = [("timeout_ns", u64), ("trace", i32), ("max_ctas", i32), ("scheduler", i32),
                 ("tile_override", i32), ("node_cost_us", C.POINTER(f32)), ("debug_never_ready", i32),
-                ("reserved", i32 * 7)]
+                ("use_graph", i32), ("autotune", i32), ("reserved", i32 * 5)]
 
 
 class dag_copy_class(C.Structure):
@@ -70,7 +70,12 @@ class dag_trace_record(C.Structure):
 class dag_plan_info(C.Structure):
     _fields_ = [("n_tiles", i32), ("n_counters", i32), ("n_waits", i32), ("grid", i32), ("smem_bytes", i32),
                 ("flops", C.c_double), ("bytes", C.c_double), ("critical_path_us", C.c_double),
-                ("work_bound_us", C.c_double)]
+                ("work_bound_us", C.c_double), ("tile_override", i32), ("scheduler", i32), ("tuned_us", C.c_double)]
+
+
+class dag_batch_item(C.Structure):
+    _fields_ = [("nodes", C.POINTER(dag_node_desc)), ("n_nodes", i32), ("buffers", C.POINTER(dag_buffer_desc)),
+                ("n_buffers", i32)]
 
 
 class DagError(RuntimeError):
@@ -85,6 +90,7 @@ _lock = threading.Lock()
 _SIGS = {
     "dag_create": (i32, [C.POINTER(dag_node_desc), C.c_int, C.POINTER(dag_edge), C.c_int,
                          C.POINTER(dag_buffer_desc), C.c_int, C.POINTER(dag_options), C.POINTER(C.c_void_p)]),
+    "dag_batch_create": (i32, [C.POINTER(dag_batch_item), C.c_int, C.POINTER(dag_options), C.POINTER(C.c_void_p)]),
     "dag_set_input": (i32, [C.c_void_p, C.c_int, C.c_void_p]),
     "dag_set_output": (i32, [C.c_void_p, C.c_int, C.c_void_p]),
     "dag_submit": (i32, [C.c_void_p, C.c_void_p]),
@@ -149,6 +155,21 @@ def dag_create(nodes, edges, buffers, options: Optional[dag_options] = None) -> 
     ba, nb = _arr(dag_buffer_desc, buffers)
     h = C.c_void_p()
     check(lib().dag_create(na, nn, ea, ne, ba, nb, C.byref(options) if options else None, C.byref(h)), "dag_create")
+    return h
+
+
+def dag_batch_create(items, options: Optional[dag_options] = None) -> C.c_void_p:
+    """items: list of (nodes, buffers) lists of ABI structs."""
+    keep = []
+    arr = (dag_batch_item * max(1, len(items)))()
+    for i, (nodes, buffers) in enumerate(items):
+        na, nn = _arr(dag_node_desc, nodes)
+        ba, nb = _arr(dag_buffer_desc, buffers)
+        keep += [na, ba]
+        arr[i] = dag_batch_item(C.cast(na, C.POINTER(dag_node_desc)), nn, C.cast(ba, C.POINTER(dag_buffer_desc)), nb)
+    h = C.c_void_p()
+    check(lib().dag_batch_create(arr, len(items), C.byref(options) if options else None, C.byref(h)),
+          "dag_batch_create")
     return h
 
 

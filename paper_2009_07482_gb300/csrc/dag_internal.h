@@ -38,6 +38,8 @@ constexpr int kStageB = kMaxBN * kBK * 2;     // 32 KiB
 constexpr int kAccCols = 256;                 // one 128 x 256 f32 accumulator
 constexpr int kTmemCols = 2 * kAccCols;       // double-buffered accumulators
 constexpr int kSlots = 2;                     // scheduler -> MMA / workers tile ring
+constexpr int kWorkerScratch = 32 * 1024;     // per-CTA worker scratch: epilogue staging / f32 tiles
+constexpr int kEpiRows = 32;                  // epilogue store box: 32 rows x 128 bytes per warp
 
 struct TileDesc {
   int32_t node;   // kernel id
@@ -69,7 +71,7 @@ struct NodeParams {
   int32_t a_dt, b_dt, c_dt, bias_dt;  // 0 = f32, 1 = bf16
   int32_t tmap_a, tmap_b;             // tensor-map indices (bf16 GEMM), else -1
   int32_t vec;                        // 16-byte vector paths are aligned
-  int32_t pad;
+  int32_t tmap_c;                     // output tensor map for the TMA-store epilogue, else -1
 };
 
 struct Ctrl {

@@ -206,12 +206,21 @@ static dag_status build_graph(const dag_node_desc *nodes, int n_nodes, const dag
         return fail(DAG_EINVAL, "node %d: unknown op %d", v, n.op);
     }
   }
-  // one writer per element, no in-place kernel
+  // writers indexed by root buffer: one writer per element, no in-place kernel
+  std::vector<std::vector<int>> writers(n_buffers);
+  for (int u = 0; u < n_nodes; ++u) writers[g.root[nodes[u].out]].push_back(u);
+  for (int r = 0; r < n_buffers; ++r) {
+    std::vector<std::pair<int, int>> iv;  // (c0, node) sorted by first column
+    for (int u : writers[r]) iv.push_back({g.full(nodes[u].out).c0, u});
+    std::sort(iv.begin(), iv.end());
+    for (size_t i = 1; i < iv.size(); ++i) {
+      const Region a = g.full(nodes[iv[i - 1].second].out), b = g.full(nodes[iv[i].second].out);
+      if (overlaps(a, b))
+        return fail(DAG_EMULTIWRITER, "nodes %d and %d write overlapping buffers", iv[i - 1].second, iv[i].second);
+    }
+  }
   for (int u = 0; u < n_nodes; ++u) {
     const Region wu = g.full(nodes[u].out);
-    for (int v = u + 1; v < n_nodes; ++v)
-      if (overlaps(wu, g.full(nodes[v].out)))
-        return fail(DAG_EMULTIWRITER, "nodes %d and %d write overlapping buffers", u, v);
     int in[3];
     const int k = g.inputs(u, in);
     for (int q = 0; q < k; ++q)
@@ -223,24 +232,21 @@ static dag_status build_graph(const dag_node_desc *nodes, int n_nodes, const dag
   for (int v = 0; v < n_nodes; ++v) {
     int in[3];
     const int k = g.inputs(v, in);
-    for (int u = 0; u < n_nodes; ++u) {
-      if (u == v) continue;
-      const Region w = g.full(nodes[u].out);
-      for (int q = 0; q < k; ++q)
-        if (overlaps(w, g.full(in[q]))) {
-          g.succ[u].push_back(v);
-          g.pred[v].push_back(u);
-          break;
-        }
-    }
-    // every element read must be written by some kernel or be an input
     for (int q = 0; q < k; ++q) {
       const Region r = g.full(in[q]);
+      for (int u : writers[r.root]) {
+        if (u == v || !overlaps(g.full(nodes[u].out), r)) continue;
+        if (std::find(g.pred[v].begin(), g.pred[v].end(), u) == g.pred[v].end()) {
+          g.pred[v].push_back(u);
+          g.succ[u].push_back(v);
+        }
+      }
+      // every element read must be written by some kernel or be an input
       if (g.bufs[r.root].flags & DAG_BUF_INPUT) continue;
       std::vector<std::pair<int, int>> cov;
-      for (int u = 0; u < n_nodes; ++u) {
+      for (int u : writers[r.root]) {
         const Region w = g.full(nodes[u].out);
-        if (w.root == r.root) cov.push_back({w.c0, w.c1});
+        cov.push_back({w.c0, w.c1});
       }
       std::sort(cov.begin(), cov.end());
       int reach = r.c0;
@@ -248,6 +254,10 @@ static dag_status build_graph(const dag_node_desc *nodes, int n_nodes, const dag
         if (c.first <= reach) reach = std::max(reach, c.second);
       if (reach < r.c1) return fail(DAG_EINVAL, "node %d reads buffer %d, which is neither an input nor fully written", v, in[q]);
     }
+  }
+  for (int v = 0; v < n_nodes; ++v) {
+    std::sort(g.succ[v].begin(), g.succ[v].end());
+    std::sort(g.pred[v].begin(), g.pred[v].end());
   }
   // edges given by the caller must be implied by the buffers
   for (int e = 0; e < n_edges; ++e) {
@@ -442,9 +452,24 @@ static void choose_configs(Plan &P) {
   }
 }
 
+// depth of every kernel in the kernel DAG (longest path from a root)
+static std::vector<int> depths(const Graph &g) {
+  std::vector<int> d(g.nn, 0);
+  for (int u : g.topo)
+    for (int v : g.succ[u]) d[v] = std::max(d[v], d[u] + 1);
+  return d;
+}
+
 static void make_tiles(Plan &P) {
   Graph &g = P.g;
   P.tiles.clear();
+  // memory-bound kernels at one depth level share the GPU: give each a share
+  // of about two tiles per SM in proportion to its elements
+  const std::vector<int> dep = depths(g);
+  std::vector<double> level_elems(g.nn + 1, 0.0);
+  for (int v = 0; v < g.nn; ++v)
+    if (g.nodes[v].op != DAG_OP_GEMM)
+      level_elems[dep[v]] += (double)g.bufs[g.nodes[v].out].rows * g.bufs[g.nodes[v].out].cols;
   P.node_first.assign(g.nn, 0);
   P.node_count.assign(g.nn, 0);
   for (int v = 0; v < g.nn; ++v) {
@@ -470,14 +495,20 @@ static void make_tiles(Plan &P) {
           for (int c = 0; c < N; c += bn)
             push(bf ? T_GEMM_BF16 : T_GEMM_F32, b * M + m, b * M + std::min(m + bm, M), c, std::min(c + bn, N), P.cfg[v]);
     } else if (n.op == DAG_OP_SOFTMAX) {
-      // 8 worker warps, two rows each in flight: 64-row tiles for short rows
-      const int rows = C <= 1024 ? 64 : 16;
+      // memory-bound and latency-bound per SM (a warp keeps two rows in
+      // flight): 16..64 rows, split further while the level has fewer than
+      // its share of two tiles per SM
+      const double share = 2.0 * P.n_sm * ((double)R * C) / std::max(1.0, level_elems[dep[v]]);
+      int rows = C <= 1024 ? 64 : 16;
+      while (rows > 16 && (double)((R + rows - 1) / rows) < share) rows /= 2;
       for (int r = 0; r < R; r += rows) push(T_SOFTMAX, r, std::min(r + rows, R), 0, C, 0);
     } else {
-      // about 32K elements per tile: enough tiles to spread a memory-bound
-      // kernel over many SMs, enough work per tile to amortise its claim
+      // at most 32K and at least 4K elements per tile, split further while
+      // the level has fewer than its share of two tiles per SM
+      const double share = 2.0 * P.n_sm * ((double)R * C) / std::max(1.0, level_elems[dep[v]]);
       int rows = 256;
-      while (rows > 8 && (long)rows * C > 32768) rows /= 2;
+      while (rows > 1 && (long)rows * C > 32768) rows /= 2;
+      while (rows > 1 && (double)((R + rows - 1) / rows) < share && (long)(rows / 2) * C >= 4096) rows /= 2;
       for (int r = 0; r < R; r += rows)
         push(n.op == DAG_OP_ADD ? T_ADD : T_UNARY, r, std::min(r + rows, R), 0, C, 0);
     }
@@ -776,10 +807,18 @@ struct dag_handle {
   bool in_flight = false, reading = false;
   dag_status poisoned = DAG_OK;
   int last_mode = 0;
+  // CUDA graph of the persistent launch (use_graph)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  double tuned_us = 0.0;
 };
 
 static void free_handle(dag_handle *h) {
   if (!h) return;
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->arena) cudaFree(h->arena);
   if (h->meta) cudaFree(h->meta);
   for (auto &s : h->up)
@@ -805,9 +844,26 @@ static dag_status encode_map(CUtensorMap *m, const void *base, uint64_t d0, uint
   return DAG_OK;
 }
 
-extern "C" dag_status dag_create(const dag_node_desc *nodes, int n_nodes, const dag_edge *edges, int n_edges,
-                                 const dag_buffer_desc *buffers, int n_buffers, const dag_options *opts,
-                                 dag_handle **out) {
+// Output map of the TMA-store epilogue: dims {N, M, batch}, box {128 bytes of
+// columns, 32 rows, 1}, 128-byte swizzle (the layout the epilogue stages).
+static dag_status encode_out_map(CUtensorMap *m, const void *base, int dtype, uint64_t N, uint64_t M, uint64_t B,
+                                 uint64_t ld_elems) {
+  const int es = esize(dtype);
+  const cuuint64_t dims[3] = {N, M, B};
+  const cuuint64_t strides[2] = {ld_elems * es, M * ld_elems * es};
+  const cuuint32_t box[3] = {(cuuint32_t)(128 / es), (cuuint32_t)kEpiRows, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = p_encode_tiled(m, dtype == DAG_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                              3, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(DAG_EUNSUPPORTED, "cuTensorMapEncodeTiled (output) failed (%d)", (int)r);
+  return DAG_OK;
+}
+
+static dag_status create_impl(const dag_node_desc *nodes, int n_nodes, const dag_edge *edges, int n_edges,
+                              const dag_buffer_desc *buffers, int n_buffers, const dag_options *opts,
+                              dag_handle **out) {
   if (!out) return fail(DAG_EINVAL, "null output handle");
   *out = nullptr;
   dag_status s = init_driver();
@@ -864,7 +920,7 @@ extern "C" dag_status dag_create(const dag_node_desc *nodes, int n_nodes, const 
     q.c_dt = g.bufs[n.out].dtype;
     q.M = g.M[v]; q.N = g.N[v]; q.K = g.K[v]; q.batch = n.op == DAG_OP_GEMM ? n.batch : 1;
     q.trans_b = n.trans_b; q.act = n.act; q.scale = n.scale;
-    q.tmap_a = q.tmap_b = -1;
+    q.tmap_a = q.tmap_b = q.tmap_c = -1;
     // 16-byte vector paths: every operand's view offset is 16-byte aligned
     // (row pitches are multiples of 16 elements by construction)
     bool vec = true;
@@ -886,6 +942,12 @@ extern "C" dag_status dag_create(const dag_node_desc *nodes, int n_nodes, const 
       if (s) { free_handle(h); return s; }
       q.tmap_a = (int)maps.size(); maps.push_back(ma);
       q.tmap_b = (int)maps.size(); maps.push_back(mb);
+      q.tmap_c = -1;
+      if ((uintptr_t)q.C % 16 == 0) {
+        CUtensorMap mc;
+        if ((s = encode_out_map(&mc, q.C, q.c_dt, N, M, B, q.ldc))) { free_handle(h); return s; }
+        q.tmap_c = (int)maps.size(); maps.push_back(mc);
+      }
     }
   }
 
@@ -946,6 +1008,85 @@ extern "C" dag_status dag_create(const dag_node_desc *nodes, int n_nodes, const 
   if (cudaDeviceSynchronize() != cudaSuccess) { free_handle(h); return fail(DAG_EDEVICE, "setup: %s", cudaGetErrorString(cudaGetLastError())); }
   *out = h;
   return DAG_OK;
+}
+
+// Median device time (us) of `runs` fine-grained submissions of h on `st`.
+static dag_status time_handle(dag_handle *h, cudaStream_t st, int runs, double *us);
+
+// The autotuner: plans with each tile policy (the concurrency heuristic, or
+// every bf16 GEMM at BN = 256 / 128) and each queue order (ranked, FIFO) are
+// built and timed on the device (zeroed buffers, one warm-up, median of three
+// runs); the fastest is kept.  The shape search is empirical: whatever the
+// time model says, the measured plan wins.
+extern "C" dag_status dag_create(const dag_node_desc *nodes, int n_nodes, const dag_edge *edges, int n_edges,
+                                 const dag_buffer_desc *buffers, int n_buffers, const dag_options *opts,
+                                 dag_handle **out) {
+  if (!opts || !opts->autotune) return create_impl(nodes, n_nodes, edges, n_edges, buffers, n_buffers, opts, out);
+  dag_options best = *opts, cand = *opts;
+  best.autotune = cand.autotune = 0;
+  cand.trace = 0;
+  cand.use_graph = 0;
+  double best_us = 1e300;
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return fail(DAG_EDEVICE, "stream");
+  const int tiles[3] = {0, 256, 128};
+  const int scheds[2] = {DAG_SCHED_RANK_MODEL, DAG_SCHED_FIFO};
+  for (int ti = 0; ti < 3; ++ti)
+    for (int si = 0; si < 2; ++si) {
+      cand.tile_override = tiles[ti];
+      cand.scheduler = scheds[si];
+      if (opts->scheduler == DAG_SCHED_RANK_GIVEN && si == 0) cand.scheduler = DAG_SCHED_RANK_GIVEN;
+      dag_handle *h = nullptr;
+      dag_status s = create_impl(nodes, n_nodes, edges, n_edges, buffers, n_buffers, &cand, &h);
+      if (s) { cudaStreamDestroy(st); return s; }
+      double us = 0;
+      s = time_handle(h, st, 3, &us);
+      free_handle(h);
+      if (s) { cudaStreamDestroy(st); return s; }
+      if (us < best_us) {
+        best_us = us;
+        best.tile_override = cand.tile_override;
+        best.scheduler = cand.scheduler;
+      }
+    }
+  cudaStreamDestroy(st);
+  dag_status s = create_impl(nodes, n_nodes, edges, n_edges, buffers, n_buffers, &best, out);
+  if (!s) (*out)->tuned_us = best_us;
+  return s;
+}
+
+extern "C" dag_status dag_batch_create(const dag_batch_item *items, int n_items, const dag_options *opts,
+                                       dag_handle **out) {
+  if (!out || n_items < 0 || (n_items && !items)) return fail(DAG_EINVAL, "bad batch arguments");
+  std::vector<dag_node_desc> nodes;
+  std::vector<dag_buffer_desc> bufs;
+  for (int i = 0; i < n_items; ++i) {
+    const dag_batch_item &it = items[i];
+    if (it.n_nodes < 0 || it.n_buffers < 0 || (it.n_nodes && !it.nodes) || (it.n_buffers && !it.buffers))
+      return fail(DAG_EINVAL, "batch item %d: bad arrays", i);
+    const int boff = (int)bufs.size();
+    for (int b = 0; b < it.n_buffers; ++b) {
+      dag_buffer_desc d = it.buffers[b];
+      if (d.view_of >= 0) {
+        if (d.view_of >= it.n_buffers) return fail(DAG_EINVAL, "batch item %d buffer %d: bad view parent", i, b);
+        d.view_of += boff;
+      }
+      bufs.push_back(d);
+    }
+    for (int v = 0; v < it.n_nodes; ++v) {
+      dag_node_desc n = it.nodes[v];
+      auto remap = [&](int32_t &id) -> bool {
+        if (id < 0) return true;
+        if (id >= it.n_buffers) return false;
+        id += boff;
+        return true;
+      };
+      if (!remap(n.a) || !remap(n.b) || !remap(n.bias) || !remap(n.out))
+        return fail(DAG_EINVAL, "batch item %d node %d: buffer id out of range", i, v);
+      nodes.push_back(n);
+    }
+  }
+  return dag_create(nodes.data(), (int)nodes.size(), nullptr, 0, bufs.data(), (int)bufs.size(), opts, out);
 }
 
 static dag_status check_handle(dag_handle *h) {
@@ -1029,7 +1170,19 @@ extern "C" dag_status dag_submit(dag_handle *h, void *stream_) {
     }
   }
   if (P.opt.trace && P.tiles.size()) CUDA_TRY(cudaMemsetAsync(h->d_trace, 0, P.tiles.size() * sizeof(TraceRec), stream));
-  if (P.tiles.size()) CUDA_TRY(launch_persistent(h->xp, P.grid, stream));
+  if (P.tiles.size() && P.opt.use_graph) {
+    if (!h->gexec) {  // capture the persistent launch once; replays reuse it
+      if (!h->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+      CUDA_TRY(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+      const cudaError_t le = launch_persistent(h->xp, P.grid, h->cap_stream);
+      const cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &h->graph);
+      if (le != cudaSuccess || ce != cudaSuccess) return fail(DAG_EDEVICE, "graph capture failed");
+      CUDA_TRY(cudaGraphInstantiate(&h->gexec, h->graph, 0));
+    }
+    CUDA_TRY(cudaGraphLaunch(h->gexec, stream));
+  } else if (P.tiles.size()) {
+    CUDA_TRY(launch_persistent(h->xp, P.grid, stream));
+  }
   CUDA_TRY(cudaEventRecord(h->ev_done, stream));
   if ((s = enqueue_readbacks(h, stream))) return s;
   h->epoch++;
@@ -1089,6 +1242,29 @@ extern "C" dag_status dag_wait(dag_handle *h, uint64_t timeout_ns) {
     h->poisoned = c.err_code == E_DEP_TIMEOUT || c.err_code == E_PIPE_TIMEOUT ? DAG_ETIMEOUT : DAG_EDEVICE;
     return fail(h->poisoned, "device error %u at tile %u", c.err_code, c.err_tile);
   }
+  return DAG_OK;
+}
+
+static dag_status time_handle(dag_handle *h, cudaStream_t st, int runs, double *us) {
+  cudaEvent_t a, b;
+  CUDA_TRY(cudaEventCreate(&a));
+  CUDA_TRY(cudaEventCreate(&b));
+  std::vector<float> ms;
+  dag_status s = DAG_OK;
+  for (int r = 0; r <= runs && !s; ++r) {
+    cudaEventRecord(a, st);
+    if ((s = dag_submit(h, st))) break;
+    cudaEventRecord(b, st);
+    if ((s = dag_wait(h, 60ull * 1000000000ull))) break;
+    float t = 0;
+    cudaEventElapsedTime(&t, a, b);
+    if (r) ms.push_back(t);  // the first run warms up
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (s) return s;
+  std::sort(ms.begin(), ms.end());
+  *us = ms.empty() ? 0.0 : ms[ms.size() / 2] * 1e3;
   return DAG_OK;
 }
 
@@ -1176,6 +1352,9 @@ extern "C" dag_status dag_plan_get(dag_handle *h, dag_plan_info *o) {
   o->bytes = h->P.bytes;
   o->critical_path_us = h->P.cp_us;
   o->work_bound_us = h->P.work_us;
+  o->tile_override = h->P.opt.tile_override;
+  o->scheduler = h->P.opt.scheduler;
+  o->tuned_us = h->tuned_us;
   return DAG_OK;
 }
 
@@ -1254,7 +1433,7 @@ dag_status dagx::plan_into_region(const dag_node_desc *nodes, int n_nodes, const
     q.c_dt = g.bufs[n.out].dtype;
     q.M = g.M[v]; q.N = g.N[v]; q.K = g.K[v]; q.batch = n.op == DAG_OP_GEMM ? n.batch : 1;
     q.trans_b = n.trans_b; q.act = n.act; q.scale = n.scale;
-    q.tmap_a = q.tmap_b = -1;
+    q.tmap_a = q.tmap_b = q.tmap_c = -1;
     bool vec = true;
     int in[3];
     const int k = g.inputs(v, in);
@@ -1272,6 +1451,12 @@ dag_status dagx::plan_into_region(const dag_node_desc *nodes, int n_nodes, const
       if (s) return s;
       q.tmap_a = (int)maps.size(); maps.push_back(ma);
       q.tmap_b = (int)maps.size(); maps.push_back(mb);
+      q.tmap_c = -1;
+      if ((uintptr_t)q.C % 16 == 0) {
+        CUtensorMap mc;
+        if ((s = encode_out_map(&mc, q.C, q.c_dt, N, M, B, q.ldc))) return s;
+        q.tmap_c = (int)maps.size(); maps.push_back(mc);
+      }
     }
   }
   // layout inside the region; counters, flags and control block start at zero

@@ -30,7 +30,7 @@ namespace dagx {
 
 constexpr int kSmemStages = kStages * (kStageA + kStageB);
 constexpr int kSmemCtl = (int)((sizeof(SmemCtl) + 255) / 256 * 256);
-constexpr int kSmemBytes = kSmemStages + kF32Smem + kSmemCtl + 1024;  // + alignment slack
+constexpr int kSmemBytes = kSmemStages + kWorkerScratch + kSmemCtl + 1024;  // + alignment slack
 static_assert(kSmemBytes <= 232448, "shared memory budget");
 
 // worker-side broadcast values (written by the worker leader)
@@ -207,7 +207,7 @@ __device__ __forceinline__ void run_workers(const ExecParams &p, uint8_t *smem, 
         ok = ws->ok != 0;
         if (ok) {
           tc_fence_after();
-          gemm_epilogue(td, np, ctl, ctl->tmem_base + accb * kAccCols);
+          gemm_epilogue(p, td, np, ctl, ctl->tmem_base + accb * kAccCols, smem + kSmemStages);
         }
         tc_fence_before();
         break;
@@ -255,7 +255,7 @@ __device__ __forceinline__ void run_workers(const ExecParams &p, uint8_t *smem, 
 __global__ void __launch_bounds__(kThreads, 1) dag_exec_kernel(const __grid_constant__ ExecParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  SmemCtl *ctl = reinterpret_cast<SmemCtl *>(smem + kSmemStages + kF32Smem);
+  SmemCtl *ctl = reinterpret_cast<SmemCtl *>(smem + kSmemStages + kWorkerScratch);
   __shared__ WorkerShared ws;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 

@@ -139,26 +139,82 @@ __device__ __forceinline__ bool gemm_mma(const TileDesc &t, const NodeParams &np
 
 // Epilogue (workers): TMEM accumulator -> scale, bias, activation, cast ->
 // global.  Worker warp w reads TMEM lanes 32*(w%4).. and the columns of half
-// (w-4)/4 of the tile; each thread owns one output row.
-__device__ __forceinline__ void gemm_epilogue(const TileDesc &t, const NodeParams &npg, const SmemCtl *ctl,
-                                              uint32_t tmem_acc) {
+// (w-4)/4 of the tile; each thread owns one output row.  With an output
+// tensor map, the two warps of a quadrant take alternate 128-byte column
+// chunks of their 32 rows and write each through a
+// 128-byte-swizzled shared staging block (one TMA store per chunk, clipped at
+// the buffer's edges); otherwise it stores directly.
+__device__ __forceinline__ void gemm_epilogue(const ExecParams &p, const TileDesc &t, const NodeParams &npg,
+                                              const SmemCtl *ctl, uint32_t tmem_acc, uint8_t *scratch) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int BN = t.cfg;
   const int M = npg.M, N = npg.N;
-  const int act = npg.act, c_dt = npg.c_dt, vec = npg.vec;
+  const int act = npg.act, c_dt = npg.c_dt, vec = npg.vec, tmap_c = npg.tmap_c;
   const float scale = npg.scale;
   void *const Cp = npg.C;
   const int64_t ldc = npg.ldc;
   const int bt = t.r0 / M, m0 = t.r0 - bt * M, n0 = t.c0;
   const int quad = warp & 3;
-  const int half = (warp - kWorkerBase / 32) >> 2;
+  const int wid = (threadIdx.x - kWorkerBase) >> 5;
+  const int half = wid >> 2;
+  const int cw = BN / 2;
+  const uint32_t trow = tmem_acc + ((uint32_t)(quad * 32) << 16);
+  if (tmap_c >= 0) {
+    const CUtensorMap *mc = p.tmaps + tmap_c;
+    uint8_t *stg = scratch + wid * (kEpiRows * 128);          // 4 KiB, 1024-aligned
+    uint8_t *myrow = stg + lane * 128;
+    const int step = c_dt == 1 ? 64 : 32;                       // columns per 128-byte row chunk
+    // the two warps of a TMEM lane quadrant take alternate whole chunks
+    // (a 64-column tile has a single bf16 chunk: the second warp idles)
+    for (int c = half * step; c < BN; c += 2 * step) {
+      if (lane == 0) bulk_wait_read();  // the previous chunk's store has left the staging block
+      __syncwarp();
+      for (int sub = 0; sub < step; sub += 32) {
+        float v[32];
+        tmem_ld32(trow + (uint32_t)(c + sub), v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = activate(act, fmaf(v[i], scale, ctl->bias[c + sub + i]));
+        // 16-byte chunk j of this row goes to position j ^ (row % 8) (128-byte swizzle)
+        if (c_dt == 1) {
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            const int j = (sub >> 3) + jj;  // sub = 0 -> chunks 0..3, sub = 32 -> chunks 4..7
+            uint4 q;
+            q.x = (uint32_t)f32_to_bf16(v[8 * jj + 0]) | ((uint32_t)f32_to_bf16(v[8 * jj + 1]) << 16);
+            q.y = (uint32_t)f32_to_bf16(v[8 * jj + 2]) | ((uint32_t)f32_to_bf16(v[8 * jj + 3]) << 16);
+            q.z = (uint32_t)f32_to_bf16(v[8 * jj + 4]) | ((uint32_t)f32_to_bf16(v[8 * jj + 5]) << 16);
+            q.w = (uint32_t)f32_to_bf16(v[8 * jj + 6]) | ((uint32_t)f32_to_bf16(v[8 * jj + 7]) << 16);
+            *reinterpret_cast<uint4 *>(myrow + ((j ^ (lane & 7)) << 4)) = q;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const uint4 q = make_uint4(__float_as_uint(v[4 * j]), __float_as_uint(v[4 * j + 1]),
+                                       __float_as_uint(v[4 * j + 2]), __float_as_uint(v[4 * j + 3]));
+            *reinterpret_cast<uint4 *>(myrow + ((j ^ (lane & 7)) << 4)) = q;
+          }
+        }
+      }
+      fence_proxy_async_shared();       // generic shared writes -> visible to the TMA engine
+      __syncwarp();
+      if (lane == 0 && n0 + c < N) {
+        tma_store_3d(mc, stg, n0 + c, m0 + quad * 32, bt);
+        bulk_commit();
+      }
+    }
+    if (lane == 0) {
+      bulk_wait_all();                  // stores complete before the tile is released
+      fence_proxy_async_global();
+    }
+    __syncwarp();
+    return;
+  }
   const int row = m0 + quad * 32 + lane;
   const bool row_ok = row < M;
   const int64_t grow = (int64_t)bt * M + row;
-  const int cw = BN / 2;
   for (int c = half * cw; c < (half + 1) * cw; c += 32) {
     float v[32];
-    tmem_ld32(tmem_acc + ((uint32_t)(quad * 32) << 16) + (uint32_t)c, v);
+    tmem_ld32(trow + (uint32_t)c, v);
     const int col = n0 + c;
     if (col >= N || !row_ok) continue;
 #pragma unroll
@@ -198,16 +254,22 @@ __device__ __forceinline__ void stage_bias(const TileDesc &t, const NodeParams &
 
 // ---------------------------------------------------------------------------
 // f32 GEMM tile, exact f32 (SIMT FFMA), BM x BN on the 256 workers as 16 x 16
-// threads, BK = 8, double-buffered shared memory.  Each thread owns a
-// (BM/16) x (BN/16) block split into 4-wide groups 64 apart, so shared reads
-// are conflict-free.
+// threads, double-buffered shared memory with register prefetch of the next
+// K slice (BK = 16, or 8 for 128 x 128 to fit the worker scratch).  Each
+// thread owns a (BM/16) x (BN/16) block split into 4-wide groups 64 apart, so
+// shared reads are conflict-free.
 // ---------------------------------------------------------------------------
-constexpr int kF32BK = 8;
-constexpr int kF32Smem = 2 * kF32BK * (128 + 4) * 4 * 2;  // bytes, for BM = BN = 128
+template <int BM, int BN>
+__host__ __device__ constexpr int f32_bk() { return (BM == 128 && BN == 128) ? 8 : 16; }
+template <int BM, int BN>
+__host__ __device__ constexpr int f32_smem() { return 2 * f32_bk<BM, BN>() * ((BM + 4) + (BN + 4)) * 4; }
+static_assert(f32_smem<128, 128>() <= kWorkerScratch && f32_smem<128, 64>() <= kWorkerScratch &&
+                  f32_smem<64, 64>() <= kWorkerScratch,
+              "f32 tile scratch");
 
 template <int BM, int BN>
 __device__ __forceinline__ void tile_gemm_f32(const TileDesc &t, const NodeParams &npg, float *smem) {
-  constexpr int BK = kF32BK;
+  constexpr int BK = f32_bk<BM, BN>();
   constexpr int TM = BM / 16, TN = BN / 16;
   constexpr int LDA_S = BM + 4, LDB_S = BN + 4;
   float *As = smem;                      // [2][BK][LDA_S]
@@ -226,24 +288,19 @@ __device__ __forceinline__ void tile_gemm_f32(const TileDesc &t, const NodeParam
   const float *B = static_cast<const float *>(npg.B) + (int64_t)bt * (trans_b ? (int64_t)N * ldb : (int64_t)K * ldb);
 
   // loader mapping: each thread moves EA (EB) consecutive elements of one row
-  constexpr int EA = BM * BK / kWorkers;      // 2 or 4
-  constexpr int EB = BN * BK / kWorkers;      // 2 or 4
+  constexpr int EA = BM * BK / kWorkers;      // 4 or 8
+  constexpr int EB = BN * BK / kWorkers;      // 4 or 8
   float ra[EA], rb[EB];
 
   auto load_run = [&](float *dst, const float *src, int n, auto en_tag) {
-    constexpr int EN = decltype(en_tag)::value;
-    if constexpr (EN == 4) {
-      if (vec && n >= 4) {
-        const float4 v = __ldcg(reinterpret_cast<const float4 *>(src));
-        dst[0] = v.x; dst[1] = v.y; dst[2] = v.z; dst[3] = v.w;
-        return;
+    constexpr int EN = decltype(en_tag)::value;  // 4 or 8: whole float4s
+    if (vec && n >= EN) {
+#pragma unroll
+      for (int q = 0; q < EN / 4; ++q) {
+        const float4 v = __ldcg(reinterpret_cast<const float4 *>(src) + q);
+        dst[4 * q] = v.x; dst[4 * q + 1] = v.y; dst[4 * q + 2] = v.z; dst[4 * q + 3] = v.w;
       }
-    } else {
-      if (vec && n >= 2) {
-        const float2 v = __ldcg(reinterpret_cast<const float2 *>(src));
-        dst[0] = v.x; dst[1] = v.y;
-        return;
-      }
+      return;
     }
 #pragma unroll
     for (int i = 0; i < EN; ++i) dst[i] = i < n ? __ldcg(src + i) : 0.f;

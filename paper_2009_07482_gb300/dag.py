@@ -56,13 +56,31 @@ def options(**kw) -> abi.dag_options:
 class Dag:
     """One created DAG on the current CUDA device."""
 
-    def __init__(self, w, opts: Optional[abi.dag_options] = None, resident_inputs: bool = False, streamed=None):
+    def __init__(self, w, opts: Optional[abi.dag_options] = None, resident_inputs: bool = False, streamed=None,
+                 _handle=None):
         self.w = w
-        nodes, edges, bufs = describe(w, resident_inputs, streamed)
         self._opts = opts
-        self.h = abi.dag_create(nodes, edges, bufs, opts)
+        if _handle is None:
+            nodes, edges, bufs = describe(w, resident_inputs, streamed)
+            _handle = abi.dag_create(nodes, edges, bufs, opts)
+        self.h = _handle
         self._keep: Dict[int, np.ndarray] = {}
         self._pinned = []
+
+    @classmethod
+    def batch(cls, workloads, opts: Optional[abi.dag_options] = None, resident_inputs: bool = False,
+              streamed=None):
+        """Many DAGs in one plan and one persistent launch (dag_batch_create).
+        Buffer ids (also in `streamed`) follow synth.workloads.concat(workloads)."""
+        from synth.workloads import concat
+        items, off = [], 0
+        for w in workloads:
+            local = None if streamed is None else {i - off for i in streamed if off <= i < off + len(w.buffers)}
+            nodes, _, bufs = describe(w, resident_inputs, local)
+            items.append((nodes, bufs))
+            off += len(w.buffers)
+        h = abi.dag_batch_create(items, opts)
+        return cls(concat(workloads), opts, _handle=h)
 
     # -- data -------------------------------------------------------------
     def set_inputs(self, inputs: Dict[int, np.ndarray], pinned: bool = False) -> None:

@@ -14,6 +14,11 @@ consecutive uniforms in (0,1].
 """
 from __future__ import annotations
 
+import ctypes as _C
+import os as _os
+import subprocess as _sp
+import threading as _th
+
 import numpy as np
 
 GOLDEN = np.uint64(0x9E3779B97F4A7C15)
@@ -91,3 +96,44 @@ def storage_to_f64(a: np.ndarray, dtype: str) -> np.ndarray:
 
 def np_storage_dtype(dtype: str):
     return np.float32 if dtype == F32 else np.uint16
+
+
+# ---------------------------------------------------------------------------
+# fast fill (C, multithreaded) with the same definitions, straight to storage
+# ---------------------------------------------------------------------------
+_HERE = _os.path.dirname(_os.path.abspath(__file__))
+_GEN_SRC = _os.path.join(_HERE, "_gen.c")
+_GEN_LIB = _os.path.join(_HERE, "_build", "libsynthgen.so")
+_gen = None
+_gen_lock = _th.Lock()
+
+
+def build(force: bool = False) -> str:
+    _os.makedirs(_os.path.dirname(_GEN_LIB), exist_ok=True)
+    if force or not _os.path.exists(_GEN_LIB) or _os.path.getmtime(_GEN_LIB) < _os.path.getmtime(_GEN_SRC):
+        tmp = _GEN_LIB + f".{_os.getpid()}.tmp"
+        _sp.check_call(["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-pthread", _GEN_SRC,
+                        "-o", tmp, "-lm"])
+        _os.replace(tmp, _GEN_LIB)
+    return _GEN_LIB
+
+
+def _lib():
+    global _gen
+    with _gen_lock:
+        if _gen is None:
+            L = _C.CDLL(build())
+            L.synth_fill.argtypes = [_C.c_int, _C.c_uint64, _C.c_double, _C.c_double, _C.c_int64, _C.c_int,
+                                     _C.c_void_p, _C.c_int]
+            L.synth_fill.restype = _C.c_int
+            _gen = L
+    return _gen
+
+
+def fill(kind: str, seed: int, shape, dtype: str, a: float, b: float = 0.0) -> np.ndarray:
+    """Storage array (f32, or bf16 bits) of uniform(lo=a, hi=b) or normal(std=a) draws."""
+    n = int(np.prod(shape))
+    out = np.empty(n, np_storage_dtype(dtype))
+    _lib().synth_fill(0 if kind == "uniform" else 1, seed & 0xFFFFFFFFFFFFFFFF, float(a), float(b), n,
+                      1 if dtype == BF16 else 0, out.ctypes.data, min(32, _os.cpu_count() or 1))
+    return out.reshape(shape)

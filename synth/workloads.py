@@ -33,7 +33,7 @@ from typing import Dict, List, Optional, Tuple
 
 import numpy as np
 
-from . import BF16, F32, normal, to_storage, uniform
+from . import BF16, F32, fill, normal, to_storage, uniform
 
 
 @dataclass
@@ -98,14 +98,13 @@ class Workload:
                 continue
             kind = b.init[0]
             if kind == "uniform":
-                x = uniform(b.init[1], (b.rows, b.cols))
+                out[i] = fill("uniform", b.init[1], (b.rows, b.cols), b.dtype, -1.0, 1.0)
             elif kind == "normal":
-                x = normal(b.init[1], (b.rows, b.cols), b.init[2])
+                out[i] = fill("normal", b.init[1], (b.rows, b.cols), b.dtype, b.init[2])
             elif kind == "array":
-                x = np.asarray(b.init[1], dtype=np.float64).reshape(b.rows, b.cols)
+                out[i] = to_storage(np.asarray(b.init[1], dtype=np.float64).reshape(b.rows, b.cols), b.dtype)
             else:
                 raise ValueError(kind)
-            out[i] = to_storage(x, b.dtype)
             if cache is not None and key is not None:
                 cache[key] = out[i]
         return out
@@ -389,3 +388,31 @@ def from_arrays(name: str, inputs: Dict[str, Tuple[np.ndarray, str]]) -> Tuple[W
         arr = np.atleast_2d(np.asarray(arr, dtype=np.float64))
         ids[nm] = w.buf(arr.shape[0], arr.shape[1], dt, "input", ("array", arr), nm)
     return w, ids
+
+
+def concat(workloads: List[Workload], name: str = "batch") -> Workload:
+    """One workload holding several DAGs side by side (ids offset in order),
+    matching the buffer and node numbering of a batched plan."""
+    w = Workload(name)
+    for x in workloads:
+        boff = len(w.buffers)
+        for b in x.buffers:
+            nb = dataclasses.replace(b)
+            if nb.view_of >= 0:
+                nb.view_of += boff
+            w.buffers.append(nb)
+        for n in x.nodes:
+            nn = dataclasses.replace(n)
+            nn.a += boff
+            nn.out += boff
+            if nn.b >= 0:
+                nn.b += boff
+            if nn.bias >= 0:
+                nn.bias += boff
+            w.nodes.append(nn)
+    return w
+
+
+def random_batch(n_dags: int = 256, base_seed: int = 1000, **kw) -> List[Workload]:
+    """The batched workload: seeded random layered DAGs, seed base_seed + i."""
+    return [random_layered(base_seed + i, **kw) for i in range(n_dags)]

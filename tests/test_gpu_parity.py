@@ -83,8 +83,10 @@ def test_gemm(case):
 
 @pytest.mark.parametrize("bn", [64, 128, 256])
 @pytest.mark.parametrize("trans_b", [0, 1])
-def test_gemm_bf16_every_tile_width(bn, trans_b):
-    w = _gemm_case(384, 640, 448, BF16, trans_b=trans_b, act="relu")
+@pytest.mark.parametrize("out_dt", [F32, BF16])
+def test_gemm_bf16_every_tile_width(bn, trans_b, out_dt):
+    # N = 600: a ragged last n-tile for every width; every output chunk width
+    w = _gemm_case(384, 600, 448, BF16, trans_b=trans_b, act="relu", out_dt=out_dt)
     _roundtrip(w, options(trace=1, tile_override=bn), coarse_too=False)
 
 

@@ -40,6 +40,14 @@ def test_uniform_normal_moments():
     assert np.array_equal(synth.uniform(7, (100,)), synth.uniform(7, (100,)))
 
 
+def test_fast_fill_matches_the_numpy_definitions():
+    for dt in (F32, BF16):
+        assert np.array_equal(synth.fill("uniform", 77, (300, 333), dt, -1.0, 1.0),
+                              synth.to_storage(synth.uniform(77, (300, 333)), dt))
+        assert np.array_equal(synth.fill("normal", 78, (300, 333), dt, 0.02),
+                              synth.to_storage(synth.normal(78, (300, 333), 0.02), dt))
+
+
 def test_bf16_rounding_hand_cases():
     g = load_golden("bf16_rounding.json")
     for (label, hexbits), v in zip(g["cases"], g["values"]):
