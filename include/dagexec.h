@@ -250,6 +250,37 @@ dag_status dag_run_noalloc(const dag_node_desc *nodes, int n_nodes, const dag_bu
                            void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* Learned cost model                                                        */
+/* ------------------------------------------------------------------------ */
+/*
+ * A 3-layer perceptron x (in_dim) -> ReLU(64) -> ReLU(64) -> 1 that predicts
+ * the (log) execution time of a kernel's tiles from its features; the
+ * predictions become per-kernel costs (dag_options.node_cost_us with
+ * DAG_SCHED_RANK_GIVEN), i.e. the bottom-level ranks that order the ready
+ * queue (paper §5: priority queue F ordered by bottom-level rank; HEFT's
+ * profiled kernel times).  Forward pass, mean-squared-error backward pass and
+ * Adam run as CUDA kernels; arrays below are host arrays (copied in and out).
+ * Parameters are one packed f32 array: W1 [in_dim][64], b1 [64], W2 [64][64],
+ * b2 [64], W3 [64], b3 [1]; they start at zero, set them with
+ * dag_mlp_set_params before training.  in_dim is 1..32.
+ */
+typedef struct dag_mlp dag_mlp;
+dag_status dag_mlp_create(int in_dim, dag_mlp **out);
+int dag_mlp_param_count(const dag_mlp *m);
+dag_status dag_mlp_set_params(dag_mlp *m, const float *params, int n);
+dag_status dag_mlp_get_params(dag_mlp *m, float *params, int n);
+/* loss = mean over the n samples of (f(x_i) - y_i)^2; grad = d loss / d params
+ * (X: n x in_dim row-major, y: n).  Deterministic: the per-64-sample chunks
+ * are summed in index order. */
+dag_status dag_mlp_loss_grad(dag_mlp *m, const float *X, const float *y, int n, float *loss, float *grad);
+/* `steps` Adam steps (beta 0.9 / 0.999, eps 1e-8, learning rate lr) on
+ * consecutive minibatches of `batch` samples, cycling through the samples in
+ * the order given. */
+dag_status dag_mlp_train(dag_mlp *m, const float *X, const float *y, int n, int steps, int batch, float lr);
+dag_status dag_mlp_predict(dag_mlp *m, const float *X, int n, float *out);
+dag_status dag_mlp_destroy(dag_mlp *m);
+
+/* ------------------------------------------------------------------------ */
 /* Inspection                                                                */
 /* ------------------------------------------------------------------------ */
 
@@ -318,6 +349,10 @@ typedef struct {
 } dag_plan_info;
 
 dag_status dag_plan_get(dag_handle *h, dag_plan_info *out);
+
+/* Per-kernel costs (us) the plan's ranks were computed from: the roofline
+ * time model's, or node_cost_us as given; n = kernel count. */
+dag_status dag_node_costs_get(dag_handle *h, float *out, int cap, int *n);
 
 /* Per-tile static description in queue order: {node, r0, r1, c0, c1, cfg}. */
 dag_status dag_tiles_get(dag_handle *h, int32_t *out6, int cap, int *n);

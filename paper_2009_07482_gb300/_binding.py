@@ -113,6 +113,15 @@ _SIGS = {
     "dag_set_peaks": (None, [C.c_double, C.c_double, C.c_double]),
     "dag_set_device": (i32, [C.c_int]),
     "dag_trace_stamps": (i32, [C.c_void_p, C.POINTER(u64), C.c_int, C.POINTER(C.c_int)]),
+    "dag_node_costs_get": (i32, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
+    "dag_mlp_create": (i32, [C.c_int, C.POINTER(C.c_void_p)]),
+    "dag_mlp_param_count": (C.c_int, [C.c_void_p]),
+    "dag_mlp_set_params": (i32, [C.c_void_p, C.c_void_p, C.c_int]),
+    "dag_mlp_get_params": (i32, [C.c_void_p, C.c_void_p, C.c_int]),
+    "dag_mlp_loss_grad": (i32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_float), C.c_void_p]),
+    "dag_mlp_train": (i32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_float]),
+    "dag_mlp_predict": (i32, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "dag_mlp_destroy": (i32, [C.c_void_p]),
     "dag_run_noalloc": (i32, [C.POINTER(dag_node_desc), C.c_int, C.POINTER(dag_buffer_desc), C.c_int,
                               C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.POINTER(dag_options), C.c_void_p]),
 }
@@ -286,6 +295,15 @@ def dag_plan_get(h) -> dag_plan_info:
     return info
 
 
+def dag_node_costs_get(h):
+    import numpy as np
+    n = C.c_int(0)
+    check(lib().dag_node_costs_get(h, None, 0, C.byref(n)), "dag_node_costs_get")
+    out = np.empty(max(1, n.value), np.float32)
+    check(lib().dag_node_costs_get(h, out.ctypes.data, n.value, C.byref(n)), "dag_node_costs_get")
+    return out[: n.value]
+
+
 def dag_tiles_get(h):
     import numpy as np
     n = C.c_int(0)
@@ -301,3 +319,58 @@ def dag_set_device(ordinal: int) -> None:
 
 def dag_set_peaks(bf16_tflops: float, f32_tflops: float, hbm_gbs: float) -> None:
     lib().dag_set_peaks(bf16_tflops, f32_tflops, hbm_gbs)
+
+
+# learned cost model -------------------------------------------------------------
+def _f32(a):
+    import numpy as np
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def dag_mlp_create(in_dim: int):
+    h = C.c_void_p()
+    check(lib().dag_mlp_create(in_dim, C.byref(h)), "dag_mlp_create")
+    return h
+
+
+def dag_mlp_param_count(m) -> int:
+    return int(lib().dag_mlp_param_count(m))
+
+
+def dag_mlp_set_params(m, params) -> None:
+    p = _f32(params)
+    check(lib().dag_mlp_set_params(m, p.ctypes.data, p.size), "dag_mlp_set_params")
+
+
+def dag_mlp_get_params(m):
+    import numpy as np
+    p = np.empty(dag_mlp_param_count(m), np.float32)
+    check(lib().dag_mlp_get_params(m, p.ctypes.data, p.size), "dag_mlp_get_params")
+    return p
+
+
+def dag_mlp_loss_grad(m, X, y):
+    import numpy as np
+    X, y = _f32(X), _f32(y)
+    g = np.empty(dag_mlp_param_count(m), np.float32)
+    loss = C.c_float(0)
+    check(lib().dag_mlp_loss_grad(m, X.ctypes.data, y.ctypes.data, len(y), C.byref(loss), g.ctypes.data),
+          "dag_mlp_loss_grad")
+    return float(loss.value), g
+
+
+def dag_mlp_train(m, X, y, steps: int, batch: int, lr: float) -> None:
+    X, y = _f32(X), _f32(y)
+    check(lib().dag_mlp_train(m, X.ctypes.data, y.ctypes.data, len(y), steps, batch, lr), "dag_mlp_train")
+
+
+def dag_mlp_predict(m, X):
+    import numpy as np
+    X = _f32(X)
+    out = np.empty(X.shape[0], np.float32)
+    check(lib().dag_mlp_predict(m, X.ctypes.data, X.shape[0], out.ctypes.data), "dag_mlp_predict")
+    return out
+
+
+def dag_mlp_destroy(m) -> None:
+    check(lib().dag_mlp_destroy(m), "dag_mlp_destroy")

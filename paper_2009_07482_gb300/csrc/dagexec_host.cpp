@@ -1358,6 +1358,14 @@ extern "C" dag_status dag_plan_get(dag_handle *h, dag_plan_info *o) {
   return DAG_OK;
 }
 
+extern "C" dag_status dag_node_costs_get(dag_handle *h, float *out, int cap, int *n) {
+  if (!h || !n) return fail(DAG_EINVAL, "null argument");
+  const int nn = h->P.g.nn;
+  *n = nn;
+  for (int i = 0; out && i < nn && i < cap; ++i) out[i] = (float)h->P.node_cost[i];
+  return DAG_OK;
+}
+
 extern "C" dag_status dag_tiles_get(dag_handle *h, int32_t *out6, int cap, int *n) {
   if (!h || !n) return fail(DAG_EINVAL, "null argument");
   const int nt = (int)h->P.queue.size();
