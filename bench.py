@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mlp_bf16",
-                    choices=["mlp_bf16", "mlp_f32", "fork_join", "encoder", "batched"])
+                    choices=["mlp_bf16", "mlp_f32", "fork_join", "encoder", "batched", "serving"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="few steps, no side measurements (for ncu)")
     return ap.parse_args()
@@ -266,10 +266,92 @@ def traffic_for(workload):
     return None, sha
 
 
+def serving_models():
+    """The serving mix: fork-join 256^3 f32; branchy MLP bf16 at batch 1, 16,
+    256; encoder block at 1 and 2 sequences of 256 tokens."""
+    from synth.workloads import branchy_mlp, encoder_block, fork_join
+    return [fork_join(256), branchy_mlp("bf16", batch=1), branchy_mlp("bf16", batch=16),
+            branchy_mlp("bf16", batch=256), encoder_block(batch=1), encoder_block(batch=2)]
+
+
+def run_serving(args):
+    """Open-loop serving: Poisson arrivals of requests drawn from the model
+    mix, continuous admission into slots by free device memory; latency =
+    completion (outputs in host memory) minus scheduled arrival."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2009_07482_gb300 import _binding as abi
+    from paper_2009_07482_gb300 import build as libbuild
+    from paper_2009_07482_gb300.costmodel import CostModel, measure, node_costs_from_tile_times
+    from paper_2009_07482_gb300.serving import Server, activation_ids
+    from synth.workloads import random_layered
+    libbuild.build()
+    torch.cuda.set_device(0)
+    ws = serving_models()
+    weights = [w.make_inputs(_INPUTS) for w in ws]
+    n_req = 2000
+    seq = [int(x) % len(ws) for x in synth.splitmix64(3, n_req)]
+
+    # kernel costs for the slots' ranks: measured profile, and the learned model
+    prof, feats = [], []
+    for w, ins in zip(ws, weights):
+        F, med, counts, grid, _ = measure(w, ins)
+        prof.append(node_costs_from_tile_times(med, counts, grid))
+        feats.append((F, counts, grid))
+    trF, trT = [], []
+    for i in range(24):
+        rw = random_layered(5000 + i, 8, 24, 4, sizes=(64, 128, 256, 512, 1024))
+        F, t, *_ = measure(rw, rw.make_inputs(_INPUTS))
+        trF.append(F)
+        trT.append(t)
+    cm = CostModel().fit(np.concatenate(trF), np.concatenate(trT))
+    learned = [node_costs_from_tile_times(cm.predict_tile_us(F), c, g) for F, c, g in feats]
+    cm.close()
+
+    def server(costs):
+        srv = Server(ws, weights, max_slots=64, hbm_reserve_bytes=8 << 30, node_costs=costs)
+        for m, w in enumerate(ws):
+            srv.set_default_io(m, {i: weights[m][i] for i in activation_ids(w)})
+            abi.dag_server_warm(srv.s, m, 4)
+        abi.dag_server_simulate(srv.s, seq[:200], 1e7, 1)  # warm-up
+        return srv
+
+    srv = server(prof)
+    _, wall, _ = abi.dag_server_simulate(srv.s, seq, 1e9, 7)   # all at once: saturation throughput
+    sat = n_req / wall
+    sweep = []
+    for f in (0.25, 0.5, 0.75, 1.0, 1.25):
+        lat, wall, mif = abi.dag_server_simulate(srv.s, seq, f * sat, 11)
+        sweep.append({"rate_frac": f, "rate_dags_per_s": f * sat, "dags_per_s": n_req / wall,
+                      "p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
+                      "max_in_flight": mif})
+    slots = abi.dag_server_slots(srv.s)
+    srv.close()
+    compare = {}
+    for name, costs in (("profile", prof), ("learned", learned)):
+        srv = server(costs)
+        lat, wall, _ = abi.dag_server_simulate(srv.s, seq, 0.75 * sat, 13)
+        compare[name] = {"p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
+                         "dags_per_s": n_req / wall}
+        srv.close()
+    compare["learned_p99_regret"] = compare["learned"]["p99_us"] / compare["profile"]["p99_us"] - 1.0
+    line = {"metric": "DAGs/s (serving, open-loop Poisson arrivals)", "value": sat, "unit": UNIT, "n_gpus": 1,
+            "steps": n_req, "warmup": 200, "ms_per_step": 1e3 / sat, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic (seeded SplitMix64)",
+            "config": {"workload": "serving mix: " + ", ".join(w.name for w in ws), "requests": n_req,
+                       "slots_created": slots, "admission": "by free HBM (8 GiB reserve), 64 slots max"},
+            "serving": sweep, "scheduler_compare_at_0.75": compare, "gpu_launches": n_req}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serving":
+        return run_serving(args)
     import numpy as np
     import torch
 

@@ -196,6 +196,10 @@ dag_status dag_submit_coarse(dag_handle *h, void *stream);
  * word: DAG_ETIMEOUT if a device wait ran out, DAG_EDEVICE on a CUDA error. */
 dag_status dag_wait(dag_handle *h, uint64_t timeout_ns);
 
+/* dag_poll: non-blocking dag_wait: DAG_EBUSY while the last submit (with its
+ * readbacks) is still running, else what dag_wait would return. */
+dag_status dag_poll(dag_handle *h);
+
 /* dag_get_output: synchronous device->host copy of buffer `buf` (rows x cols,
  * dense) into host_ptr; call after dag_wait. */
 dag_status dag_get_output(dag_handle *h, int buf, void *host_ptr);
@@ -248,6 +252,61 @@ void dag_host_free(void *p);
 dag_status dag_run_noalloc(const dag_node_desc *nodes, int n_nodes, const dag_buffer_desc *buffers, int n_buffers,
                            void *const *buffer_ptrs, const int64_t *row_pitch, const dag_options *opts,
                            void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous admission of inference DAGs                           */
+/* ------------------------------------------------------------------------ */
+/*
+ * A model is an inference DAG at a fixed batch size: its RESIDENT inputs are
+ * weights (host data given here, uploaded once per slot and kept on the
+ * device), its other inputs are the per-request activations, its OUTPUT
+ * buffers are read back per request.  A slot is one planned instance of a
+ * model with its own device buffers and stream.  Requests are admitted in
+ * arrival order as soon as their model has an idle slot, or a new slot fits
+ * in the free device memory (less hbm_reserve_bytes) under max_slots; an
+ * admitted request launches immediately, so requests arriving while others
+ * run overlap them on the device.  node_cost_us (may be NULL) gives the
+ * per-kernel costs that rank each slot's queue (learned or measured).
+ */
+typedef struct {
+  const dag_node_desc *nodes;
+  int32_t n_nodes;
+  const dag_buffer_desc *buffers;
+  int32_t n_buffers;
+  const void *const *weights;   /* [n_buffers]: host data of every RESIDENT input, NULL elsewhere */
+  const float *node_cost_us;    /* [n_nodes] or NULL */
+} dag_model_desc;
+
+typedef struct {
+  int32_t model;
+  int32_t status;               /* dag_status of the request */
+  double t_arrive_s, t_launch_s, t_done_s;  /* steady clock, seconds */
+} dag_request_info;
+
+typedef struct dag_server dag_server;
+dag_status dag_server_create(const dag_model_desc *models, int n_models, int max_slots, size_t hbm_reserve_bytes,
+                             const dag_options *opts, dag_server **out);
+/* default request inputs/outputs of a model (streamed inputs and OUTPUT
+ * buffers in buffer order), used when dag_server_submit gets NULL */
+dag_status dag_server_set_io(dag_server *s, int model, const void *const *inputs, void *const *outputs);
+/* create up to n_slots idle slots of a model now (planning and weight upload
+ * ahead of the first requests) */
+dag_status dag_server_warm(dag_server *s, int model, int n_slots);
+/* queue a request (thread-safe); host buffers stay valid until it completes */
+dag_status dag_server_submit(dag_server *s, int model, const void *const *inputs, void *const *outputs,
+                             uint64_t *ticket);
+/* complete finished requests, admit and launch waiting ones; returns the
+ * number completed */
+int dag_server_progress(dag_server *s);
+/* drive progress until the request completes; fills info; releases the ticket */
+dag_status dag_server_wait(dag_server *s, uint64_t ticket, uint64_t timeout_ns, dag_request_info *info);
+/* open-loop run: n requests of the given models arriving as a Poisson process
+ * of rate_hz (seeded SplitMix64 exponential gaps); latency_us[i] = completion
+ * (readback done) minus scheduled arrival */
+dag_status dag_server_simulate(dag_server *s, const int32_t *model_seq, int n, double rate_hz, uint64_t seed,
+                               double *latency_us, double *wall_s, int *max_in_flight);
+int dag_server_slots(dag_server *s);
+dag_status dag_server_destroy(dag_server *s);
 
 /* ------------------------------------------------------------------------ */
 /* Learned cost model                                                        */

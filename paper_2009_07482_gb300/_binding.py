@@ -78,6 +78,16 @@ class dag_batch_item(C.Structure):
                 ("n_buffers", i32)]
 
 
+class dag_model_desc(C.Structure):
+    _fields_ = [("nodes", C.POINTER(dag_node_desc)), ("n_nodes", i32), ("buffers", C.POINTER(dag_buffer_desc)),
+                ("n_buffers", i32), ("weights", C.POINTER(C.c_void_p)), ("node_cost_us", C.POINTER(f32))]
+
+
+class dag_request_info(C.Structure):
+    _fields_ = [("model", i32), ("status", i32), ("t_arrive_s", C.c_double), ("t_launch_s", C.c_double),
+                ("t_done_s", C.c_double)]
+
+
 class DagError(RuntimeError):
     def __init__(self, status: int, where: str, msg: str):
         self.status = status
@@ -114,6 +124,19 @@ _SIGS = {
     "dag_set_device": (i32, [C.c_int]),
     "dag_trace_stamps": (i32, [C.c_void_p, C.POINTER(u64), C.c_int, C.POINTER(C.c_int)]),
     "dag_node_costs_get": (i32, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
+    "dag_poll": (i32, [C.c_void_p]),
+    "dag_server_create": (i32, [C.POINTER(dag_model_desc), C.c_int, C.c_int, C.c_size_t, C.POINTER(dag_options),
+                                C.POINTER(C.c_void_p)]),
+    "dag_server_set_io": (i32, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]),
+    "dag_server_warm": (i32, [C.c_void_p, C.c_int, C.c_int]),
+    "dag_server_submit": (i32, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                C.POINTER(C.c_uint64)]),
+    "dag_server_progress": (C.c_int, [C.c_void_p]),
+    "dag_server_wait": (i32, [C.c_void_p, C.c_uint64, C.c_uint64, C.POINTER(dag_request_info)]),
+    "dag_server_simulate": (i32, [C.c_void_p, C.POINTER(i32), C.c_int, C.c_double, C.c_uint64,
+                                  C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int)]),
+    "dag_server_slots": (C.c_int, [C.c_void_p]),
+    "dag_server_destroy": (i32, [C.c_void_p]),
     "dag_mlp_create": (i32, [C.c_int, C.POINTER(C.c_void_p)]),
     "dag_mlp_param_count": (C.c_int, [C.c_void_p]),
     "dag_mlp_set_params": (i32, [C.c_void_p, C.c_void_p, C.c_int]),
@@ -374,3 +397,76 @@ def dag_mlp_predict(m, X):
 
 def dag_mlp_destroy(m) -> None:
     check(lib().dag_mlp_destroy(m), "dag_mlp_destroy")
+
+
+# serving -----------------------------------------------------------------------
+def dag_poll(h) -> int:
+    return int(lib().dag_poll(h))
+
+
+def _ptrs(ps):
+    return (C.c_void_p * max(1, len(ps)))(*[C.c_void_p(p) if p else None for p in ps])
+
+
+def dag_server_create(models, max_slots: int, hbm_reserve_bytes: int = 0, options: Optional[dag_options] = None):
+    """models: list of (nodes, buffers, weights_ptrs, node_cost_us or None)."""
+    keep = []
+    arr = (dag_model_desc * len(models))()
+    for i, (nodes, bufs, wptrs, costs) in enumerate(models):
+        na, nn = _arr(dag_node_desc, nodes)
+        ba, nb = _arr(dag_buffer_desc, bufs)
+        wa = _ptrs(wptrs)
+        ca = (f32 * len(costs))(*costs) if costs is not None else None
+        keep += [na, ba, wa, ca]
+        arr[i] = dag_model_desc(C.cast(na, C.POINTER(dag_node_desc)), nn, C.cast(ba, C.POINTER(dag_buffer_desc)), nb,
+                                C.cast(wa, C.POINTER(C.c_void_p)),
+                                C.cast(ca, C.POINTER(f32)) if ca is not None else None)
+    h = C.c_void_p()
+    check(lib().dag_server_create(arr, len(models), max_slots, hbm_reserve_bytes,
+                                  C.byref(options) if options else None, C.byref(h)), "dag_server_create")
+    return h
+
+
+def dag_server_set_io(s, model: int, inputs, outputs) -> None:
+    check(lib().dag_server_set_io(s, model, _ptrs(inputs), _ptrs(outputs)), "dag_server_set_io")
+
+
+def dag_server_warm(s, model: int, n_slots: int) -> None:
+    check(lib().dag_server_warm(s, model, n_slots), "dag_server_warm")
+
+
+def dag_server_submit(s, model: int, inputs=None, outputs=None) -> int:
+    t = C.c_uint64(0)
+    check(lib().dag_server_submit(s, model, _ptrs(inputs) if inputs is not None else None,
+                                  _ptrs(outputs) if outputs is not None else None, C.byref(t)), "dag_server_submit")
+    return t.value
+
+
+def dag_server_progress(s) -> int:
+    return int(lib().dag_server_progress(s))
+
+
+def dag_server_wait(s, ticket: int, timeout_ns: int = 60_000_000_000):
+    info = dag_request_info()
+    check(lib().dag_server_wait(s, ticket, timeout_ns, C.byref(info)), "dag_server_wait")
+    return info
+
+
+def dag_server_simulate(s, model_seq, rate_hz: float, seed: int):
+    import numpy as np
+    n = len(model_seq)
+    ms = (i32 * n)(*model_seq)
+    lat = np.zeros(n, np.float64)
+    wall = C.c_double(0)
+    mif = C.c_int(0)
+    check(lib().dag_server_simulate(s, ms, n, rate_hz, seed, lat.ctypes.data_as(C.POINTER(C.c_double)),
+                                    C.byref(wall), C.byref(mif)), "dag_server_simulate")
+    return lat, wall.value, mif.value
+
+
+def dag_server_slots(s) -> int:
+    return int(lib().dag_server_slots(s))
+
+
+def dag_server_destroy(s) -> None:
+    check(lib().dag_server_destroy(s), "dag_server_destroy")

@@ -1268,6 +1268,15 @@ static dag_status time_handle(dag_handle *h, cudaStream_t st, int runs, double *
   return DAG_OK;
 }
 
+extern "C" dag_status dag_poll(dag_handle *h) {
+  if (!h) return fail(DAG_EINVAL, "null handle");
+  if (h->poisoned) return fail(h->poisoned, "handle poisoned by an earlier device error");
+  if (!h->in_flight) return DAG_OK;
+  const cudaError_t e = cudaEventQuery(h->reading ? h->ev_read : h->ev_done);
+  if (e == cudaErrorNotReady) return DAG_EBUSY;
+  return dag_wait(h, 0);
+}
+
 extern "C" dag_status dag_get_output(dag_handle *h, int buf, void *host_ptr) {
   dag_status s = check_handle(h);
   if (s) return s;
