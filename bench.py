@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--workload", default="mlp_bf16",
                     choices=["mlp_bf16", "mlp_f32", "fork_join", "encoder", "batched", "serving"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="batched: skip the cost-model comparison")
     ap.add_argument("--profile", action="store_true", help="few steps, no side measurements (for ncu)")
     return ap.parse_args()
 
@@ -53,7 +54,8 @@ def make_workload(name):
     """(workload, description); for "batched" the workload is the list of DAGs."""
     from synth.workloads import branchy_mlp, encoder_block, fork_join, random_batch
     if name == "batched":
-        return random_batch(256), ("256 seeded random layered DAGs (8-64 nodes, widths 1-8; GEMM 70% / eltwise 20% / "
+        rank = int(os.environ.get("RANK", 0))
+        return random_batch(256, base_seed=1000 + 256 * rank), ("256 seeded random layered DAGs (8-64 nodes, widths 1-8; GEMM 70% / eltwise 20% / "
                                    "softmax 10%; M,N,K in {64..2048}; bf16 or f32 per DAG) in one persistent launch "
                                    "replayed from a CUDA graph")
     if name == "mlp_bf16":
@@ -266,6 +268,70 @@ def traffic_for(workload):
     return None, sha
 
 
+def learned_eval_batched(wl, ins, abi, Dag, options, timed_fn):
+    """Ranks for the 256-DAG batch from three cost sources -- the planner's
+    roofline model (default), a measured profile (tile times traced on a run
+    of this batch) and the learned MLP (trained on traces of other random
+    DAGs) -- plus FIFO order; reports the median makespan of each and the
+    prediction error of the model-based sources against the profile."""
+    import numpy as np
+    from paper_2009_07482_gb300.costmodel import (CostModel, features, measure, mape,
+                                                  node_costs_from_tile_times)
+    from synth.workloads import concat
+    # profile of the batch itself
+    d = Dag.batch(wl, options(trace=1, use_graph=1), resident_inputs=True)
+    d.set_inputs(ins)
+    for _ in range(2):
+        d.run()
+    st = abi.dag_trace_stamps(d.h).astype(np.int64)
+    tiles = d.tiles()
+    grid = d.plan().grid
+    model_costs = abi.dag_node_costs_get(d.h).astype(np.float64)
+    d.close()
+    nn = sum(len(x.nodes) for x in wl)
+    dur = (st[:, 9] - st[:, 1]) / 1e3
+    per = [[] for _ in range(nn)]
+    for t, v in enumerate(tiles[:, 0]):
+        per[v].append(dur[t])
+    prof_tile = np.array([np.median(x) if x else 0.0 for x in per])
+    counts = np.bincount(tiles[:, 0], minlength=nn)
+    prof_costs = node_costs_from_tile_times(prof_tile, counts, grid)
+    model_tile = model_costs / np.ceil(np.maximum(counts, 1) / grid)
+    # learned model trained on traces of other random DAGs, alone and in
+    # batches of 2..64 (so its concurrency feature covers batched plans)
+    from synth.workloads import random_batch
+    trF, trT = [], []
+    seed = 5000
+    for k in (1, 1, 1, 1, 2, 4, 8, 16, 32, 64):
+        rw = concat(random_batch(k, base_seed=seed))
+        seed += k
+        F, t, *_ = measure(rw, rw.make_inputs(_INPUTS))
+        trF.append(F)
+        trT.append(t)
+    cm = CostModel().fit(np.concatenate(trF), np.concatenate(trT))
+    # features of each DAG inside the batch plan (level concurrency of the batch)
+    wcat = concat(wl)
+    Fb = features(wcat, tiles, grid)
+    learn_tile = cm.predict_tile_us(Fb)
+    learn_costs = node_costs_from_tile_times(learn_tile, counts, grid)
+    cm.close()
+    res = {"mape_learned_vs_profile": mape(learn_tile, prof_tile),
+           "mape_roofline_vs_profile": mape(model_tile, prof_tile), "makespan_us": {}}
+    for name, o in (("rank_roofline_model", options(use_graph=1)),
+                    ("rank_profile", options(use_graph=1, scheduler=abi.DAG_SCHED_RANK_GIVEN, node_cost_us=prof_costs)),
+                    ("rank_learned", options(use_graph=1, scheduler=abi.DAG_SCHED_RANK_GIVEN, node_cost_us=learn_costs)),
+                    ("fifo", options(use_graph=1, scheduler=abi.DAG_SCHED_FIFO))):
+        dd = Dag.batch(wl, o, resident_inputs=True)
+        dd.set_inputs(ins)
+        dd.run()
+        res["makespan_us"][name] = statistics.median(timed_fn(dd, 5))
+        dd.close()
+    ms = res["makespan_us"]
+    res["regret_learned_vs_profile"] = ms["rank_learned"] / ms["rank_profile"] - 1.0
+    res["gain_learned_vs_roofline_model"] = ms["rank_roofline_model"] / ms["rank_learned"] - 1.0
+    return res
+
+
 def serving_models():
     """The serving mix: fork-join 256^3 f32; branchy MLP bf16 at batch 1, 16,
     256; encoder block at 1 and 2 sequences of 256 tokens."""
@@ -318,6 +384,7 @@ def run_serving(args):
         return srv
 
     srv = server(prof)
+    abi.dag_server_simulate(srv.s, seq, 1e9, 5)                 # untimed: creates the slots the mix needs
     _, wall, _ = abi.dag_server_simulate(srv.s, seq, 1e9, 7)   # all at once: saturation throughput
     sat = n_req / wall
     sweep = []
@@ -522,6 +589,19 @@ def main():
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),
     }
+    if batched and not args.no_learned:
+        def timed_fn(dd, n):
+            out = []
+            for _ in range(n):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                dd.submit(sp)
+                b.record(stream)
+                abi.check(dd.wait(), "wait")
+                out.append(a.elapsed_time(b) * 1e3)
+            return out
+        line["learned"] = learned_eval_batched(wl, ins, abi, Dag, options, timed_fn)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(args.workload)
     if rank == 0:
