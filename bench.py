@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="batched: skip the cost-model comparison")
     ap.add_argument("--profile", action="store_true", help="few steps, no side measurements (for ncu)")
+    ap.add_argument("--f32-simt", action="store_true", help="f32 GEMMs on the SM cores (FFMA) instead of 3 x TF32")
     return ap.parse_args()
 
 
@@ -453,7 +454,7 @@ def main():
     Y_ids = w.output_ids()
 
     def make_dag(streamed):
-        o = options(use_graph=1 if batched else 0)
+        o = options(use_graph=1 if batched else 0, f32_gemm=abi.DAG_F32_GEMM_SIMT if args.f32_simt else 0)
         if batched:
             return Dag.batch(wl, o, resident_inputs=not streamed, streamed=set(X_ids) if streamed else None)
         return Dag(w, o, streamed=set(X_ids)) if streamed else Dag(w, o, resident_inputs=True)
@@ -544,8 +545,13 @@ def main():
     e.close()
 
     # roofline of the executor kernel (the only kernel of a step)
-    # f32 GEMMs run on the FP32 ALUs: 152 SMs x 128 FFMA/clk x 2 flop x max SM clock
-    f32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    # f32 GEMMs: the larger of the FP32 ALU peak (152 SMs x 128 FFMA/clk x 2
+    # flop x max SM clock) and the 3 x TF32 tensor peak (measured bf16 x the
+    # nominal tf32/bf16 ratio 1.1/2.25, / 3 products); the executor runs them
+    # on the tensor cores unless --f32-simt
+    simt_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    tc_peak = peaks["bf16_tflops"] * (1.1 / 2.25) / 3.0
+    f32_peak = simt_peak if args.f32_simt else max(simt_peak, tc_peak)
     fl = {"bf16": 0.0, "f32": 0.0}
     for k, n in enumerate(w.nodes):
         if n.op == "gemm":
@@ -553,11 +559,12 @@ def main():
     t_bound_us = (fl["bf16"] / peaks["bf16_tflops"] + fl["f32"] / f32_peak) / 1e6
     achieved = info.flops / (mean_us * 1e-6) / 1e12
     src_bf16 = f"{peaks_src} bf16 burst (MEASURED_PEAKS.json)" if peaks_src == "measured" else "fallback 1.9 PF/s"
-    src_f32 = "derived: 152 SMs x 128 f32 FMA/clk x 2 flop x max SM clock"
+    src_f32 = ("3 x TF32 on the tensor cores: measured bf16 burst x 1.1/2.25 (nominal tf32/bf16) / 3"
+               if f32_peak == tc_peak else "derived: 152 SMs x 128 f32 FMA/clk x 2 flop x max SM clock")
     if fl["f32"] == 0:
         roof = {"bound": "tensor", "peak": peaks["bf16_tflops"], "peak_source": src_bf16}
     elif fl["bf16"] == 0:
-        roof = {"bound": "alu", "peak": f32_peak, "peak_source": src_f32}
+        roof = {"bound": "alu" if args.f32_simt else "tensor", "peak": f32_peak, "peak_source": src_f32}
     else:
         roof = {"bound": "tensor", "peak": info.flops / t_bound_us / 1e6,
                 "peak_source": f"flop-weighted: bf16 at {src_bf16}, f32 at {src_f32}"}
@@ -577,6 +584,7 @@ def main():
         "config": {"workload": desc, "dags_per_step": n_dags, "nodes": len(w.nodes), "tiles": info.n_tiles,
                    "grid": info.grid,
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
+                   "f32_gemm": "SM cores (FFMA)" if args.f32_simt else "tensor cores (3 x TF32 split)",
                    "parallelism": f"replicas x{world} (independent DAGs per GPU)" if world > 1 else "1 GPU"},
         "makespan_us": {"median": med, "p10": float(q[0]), "p90": float(q[1]), "mean": statistics.mean(fine_us)},
         "coarse": {"median_us": cmed, "launches_per_step": n_coarse_launches,

@@ -130,8 +130,17 @@ typedef struct {
   int32_t use_graph;          /* 1: dag_submit replays the persistent launch from a captured CUDA graph */
   int32_t autotune;           /* 1: dag_create times candidate plans (tile widths x queue orders) on the
                                  device with zeroed buffers and keeps the fastest (see dag_plan_info) */
-  int32_t reserved[5];
+  int32_t f32_gemm;           /* dag_f32_gemm: how f32 GEMMs run */
+  int32_t reserved[4];
 } dag_options;
+
+/* f32 GEMM arithmetic.  DAG_F32_GEMM_TENSOR (default): on the tensor cores
+ * with the 3 x TF32 split (each operand x = hi + lo, hi = tf32(x),
+ * lo = tf32(x - hi); A.B ~= Ahi.Bhi + Ahi.Blo + Alo.Bhi with f32
+ * accumulation; about 2^-21 relative error per product), for every f32 GEMM
+ * whose operand views start on 16-byte boundaries; the others, and every f32
+ * GEMM under DAG_F32_GEMM_SIMT, run as f32 FFMA on the SM cores. */
+typedef enum { DAG_F32_GEMM_TENSOR = 0, DAG_F32_GEMM_SIMT = 1 } dag_f32_gemm;
 
 typedef struct dag_handle dag_handle;
 

@@ -26,6 +26,7 @@ DAG_OP_GEMM, DAG_OP_ADD, DAG_OP_SOFTMAX, DAG_OP_UNARY = 0, 1, 2, 3
 DAG_ACT_NONE, DAG_ACT_RELU, DAG_ACT_GELU = 0, 1, 2
 DAG_BUF_INPUT, DAG_BUF_OUTPUT, DAG_BUF_RESIDENT = 1, 2, 4
 DAG_SCHED_RANK_MODEL, DAG_SCHED_RANK_GIVEN, DAG_SCHED_FIFO = 0, 1, 2
+DAG_F32_GEMM_TENSOR, DAG_F32_GEMM_SIMT = 0, 1
 
 
 class dag_buffer_desc(C.Structure):
@@ -45,7 +46,7 @@ class dag_edge(C.Structure):
 class dag_options(C.Structure):
     _fields_ = [("timeout_ns", u64), ("trace", i32), ("max_ctas", i32), ("scheduler", i32),
                 ("tile_override", i32), ("node_cost_us", C.POINTER(f32)), ("debug_never_ready", i32),
-                ("use_graph", i32), ("autotune", i32), ("reserved", i32 * 5)]
+                ("use_graph", i32), ("autotune", i32), ("f32_gemm", i32), ("reserved", i32 * 4)]
 
 
 class dag_copy_class(C.Structure):

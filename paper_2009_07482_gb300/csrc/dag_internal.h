@@ -17,21 +17,25 @@ enum TileOp : int32_t {
   T_GEMM_F32 = 1,   // exact-f32 SIMT FFMA, BM x BN
   T_ADD = 2,        // 128-bit elementwise add (+ activation)
   T_UNARY = 3,      // 128-bit elementwise activation
-  T_SOFTMAX = 4     // warp-per-row softmax over whole rows
+  T_SOFTMAX = 4,    // warp-per-row softmax over whole rows
+  T_GEMM_TF32 = 5   // f32 GEMM on the tensor cores, 3 x TF32 split, 128 x 64
 };
 
 // f32 SIMT GEMM tile shapes (cfg field of a T_GEMM_F32 tile)
 enum F32Cfg : int32_t { F32_64x64 = 0, F32_128x64 = 1, F32_128x128 = 2 };
 
 // CTA layout: warp 0 = scheduler + TMA producer, warp 1 = MMA issuer,
-// warps 2-3 idle, warps 4-11 = 256 worker threads (GEMM epilogues and every
-// SIMT tile).
+// warps 2-3 idle, warps 4-11 = 256 worker threads (GEMM epilogues, the
+// operand split of f32 tensor-core tiles, and every SIMT tile).
 constexpr int kThreads = 384;
 constexpr int kWorkerBase = 128;    // first worker thread
 constexpr int kWorkers = 256;       // worker threads
 constexpr int kBM = 128;            // bf16 GEMM tile rows (MMA M)
 constexpr int kBK = 64;             // bf16 K per stage (one 128-byte swizzle row)
 constexpr int kStages = 4;          // TMA -> MMA pipeline depth
+constexpr int kBKF = 32;            // f32 K per stage (one 128-byte swizzle row)
+constexpr int kTf32BN = 64;         // f32 tensor-core tile width
+constexpr int kParts = 4;           // TMEM partial slots of an f32 tensor-core tile (4 x 64 columns)
 constexpr int kMaxBN = 256;
 constexpr int kStageA = kBM * kBK * 2;        // 16 KiB
 constexpr int kStageB = kMaxBN * kBK * 2;     // 32 KiB

@@ -63,6 +63,9 @@ extern "C" const char *dag_last_error(void) { return g_err.c_str(); }
 // peaks for the time model and the roofline estimates
 // ---------------------------------------------------------------------------
 static double g_bf16_tflops = 1918.4, g_f32_tflops = 60.0, g_hbm_gbs = 6695.2;
+// f32 on the tensor cores: tf32 runs at the nominal tf32 / bf16 ratio
+// (1.1 / 2.25 PFLOP/s dense) of the bf16 peak, and a 3 x TF32 product takes three
+static double tf32x3_tflops() { return g_bf16_tflops * (1.1 / 2.25) / 3.0; }
 
 extern "C" void dag_set_peaks(double bf16_tflops, double f32_tflops, double hbm_gbs) {
   if (bf16_tflops > 0) g_bf16_tflops = bf16_tflops;
@@ -357,6 +360,7 @@ struct Plan {
   dag_options opt{};
   int n_sm = 148, grid = 148;
   std::vector<int> cfg;                 // per node tile config
+  std::vector<char> tf32;               // per node: f32 GEMM on the tensor cores (3 x TF32)
   std::vector<TileDesc> tiles;          // node-major creation order
   std::vector<int> node_first, node_count;
   std::vector<TileDesc> queue;          // queue order (persistent mode)
@@ -389,6 +393,9 @@ static double tile_time_us(const Plan &P, int v, const TileDesc &t) {
     if (t.op == T_GEMM_BF16) {
       const double eff = t.cfg >= 256 ? 0.8 : t.cfg >= 128 ? 0.7 : 0.5;
       rate = g_bf16_tflops * 1e12 / P.n_sm * eff;
+    } else if (t.op == T_GEMM_TF32) {
+      // three tf32 MMAs (half the bf16 rate) per product, 128 x 64 tiles
+      rate = g_bf16_tflops * 1e12 / P.n_sm / 6.0 * 0.5;
     } else {
       rate = g_f32_tflops * 1e12 / P.n_sm * 0.6;
     }
@@ -415,6 +422,13 @@ static void choose_configs(Plan &P) {
   int maxd = 0;
   for (int v = 0; v < nn; ++v) maxd = std::max(maxd, depth[v]);
   P.cfg.assign(nn, 0);
+  P.tf32.assign(nn, 0);
+  for (int v = 0; v < nn; ++v) {
+    const dag_node_desc &n = g.nodes[v];
+    if (n.op != DAG_OP_GEMM || g.bufs[n.a].dtype != DAG_F32 || P.opt.f32_gemm == DAG_F32_GEMM_SIMT) continue;
+    // TMA operands: 16-byte aligned column views (roots and row pitches are)
+    P.tf32[v] = ((size_t)g.coff[n.a] * 4) % 16 == 0 && ((size_t)g.coff[n.b] * 4) % 16 == 0;
+  }
   static const int bns[3] = {256, 128, 64};
   static const int f32c[3][3] = {{F32_128x128, 128, 128}, {F32_128x64, 128, 64}, {F32_64x64, 64, 64}};
   for (int pass = 0; pass < 3; ++pass) {
@@ -423,7 +437,8 @@ static void choose_configs(Plan &P) {
     for (int v = 0; v < nn; ++v) {
       const dag_node_desc &n = g.nodes[v];
       if (n.op != DAG_OP_GEMM) { level[depth[v]] += 8; continue; }
-      if (g.bufs[n.a].dtype == DAG_BF16) level[depth[v]] += ntiles_gemm(g, v, 128, bns[pass]);
+      if (P.tf32[v]) level[depth[v]] += ntiles_gemm(g, v, 128, kTf32BN);
+      else if (g.bufs[n.a].dtype == DAG_BF16) level[depth[v]] += ntiles_gemm(g, v, 128, bns[pass]);
       else level[depth[v]] += ntiles_gemm(g, v, f32c[pass][1], f32c[pass][2]);
     }
     for (int v = 0; v < nn; ++v) {
@@ -431,7 +446,9 @@ static void choose_configs(Plan &P) {
       if (n.op != DAG_OP_GEMM || P.cfg[v]) continue;
       const bool enough = level[depth[v]] >= P.n_sm * 3 / 4 || pass == 2;
       if (!enough) continue;
-      if (g.bufs[n.a].dtype == DAG_BF16) {
+      if (P.tf32[v]) {
+        P.cfg[v] = kTf32BN + 100;
+      } else if (g.bufs[n.a].dtype == DAG_BF16) {
         int bn = bns[pass];
         while (bn > 64 && bn / 2 >= round_up(g.N[v], 64)) bn /= 2;  // no wider than N
         P.cfg[v] = bn;
@@ -483,8 +500,10 @@ static void make_tiles(Plan &P) {
     const int R = g.bufs[n.out].rows, C = g.bufs[n.out].cols;
     if (n.op == DAG_OP_GEMM) {
       const bool bf = g.bufs[n.a].dtype == DAG_BF16;
+      const int op = bf ? T_GEMM_BF16 : P.tf32[v] ? T_GEMM_TF32 : T_GEMM_F32;
       int bm, bn;
       if (bf) { bm = kBM; bn = P.cfg[v]; }
+      else if (P.tf32[v]) { bm = kBM; bn = kTf32BN; }
       else {
         bm = P.cfg[v] == F32_64x64 ? 64 : 128;
         bn = P.cfg[v] == F32_128x128 ? 128 : 64;
@@ -493,7 +512,7 @@ static void make_tiles(Plan &P) {
       for (int b = 0; b < n.batch; ++b)
         for (int m = 0; m < M; m += bm)
           for (int c = 0; c < N; c += bn)
-            push(bf ? T_GEMM_BF16 : T_GEMM_F32, b * M + m, b * M + std::min(m + bm, M), c, std::min(c + bn, N), P.cfg[v]);
+            push(op, b * M + m, b * M + std::min(m + bm, M), c, std::min(c + bn, N), P.cfg[v]);
     } else if (n.op == DAG_OP_SOFTMAX) {
       // memory-bound and latency-bound per SM (a warp keeps two rows in
       // flight): 16..64 rows, split further while the level has fewer than
@@ -709,7 +728,7 @@ static void roofline(Plan &P) {
     double peak;
     if (n.op == DAG_OP_GEMM) {
       f = 2.0 * n.batch * (double)g.M[v] * g.N[v] * g.K[v];
-      peak = (g.bufs[n.a].dtype == DAG_BF16 ? g_bf16_tflops : g_f32_tflops) * 1e12;
+      peak = (g.bufs[n.a].dtype == DAG_BF16 ? g_bf16_tflops : P.tf32[v] ? tf32x3_tflops() : g_f32_tflops) * 1e12;
     } else {
       f = (double)g.bufs[n.out].rows * g.bufs[n.out].cols;
       peak = 1e30;  // elementwise work is memory-bound
@@ -727,13 +746,14 @@ static void roofline(Plan &P) {
     cp = std::max(cp, fin[v]);
   }
   P.cp_us = cp;
-  double f_bf = 0, f_32 = 0;
+  double f_bf = 0, f_tc = 0, f_32 = 0;
   for (int v = 0; v < g.nn; ++v)
     if (g.nodes[v].op == DAG_OP_GEMM) {
       const double f = 2.0 * g.nodes[v].batch * (double)g.M[v] * g.N[v] * g.K[v];
-      (g.bufs[g.nodes[v].a].dtype == DAG_BF16 ? f_bf : f_32) += f;
+      (g.bufs[g.nodes[v].a].dtype == DAG_BF16 ? f_bf : P.tf32[v] ? f_tc : f_32) += f;
     }
-  const double work = (f_bf / (g_bf16_tflops * 1e12) + f_32 / (g_f32_tflops * 1e12)) * 1e6;
+  const double work =
+      (f_bf / (g_bf16_tflops * 1e12) + f_tc / (tf32x3_tflops() * 1e12) + f_32 / (g_f32_tflops * 1e12)) * 1e6;
   P.work_us = std::max(cp, std::max(work, P.bytes / (g_hbm_gbs * 1e9) * 1e6));
 }
 
@@ -832,12 +852,14 @@ static void free_handle(dag_handle *h) {
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 static dag_status encode_map(CUtensorMap *m, const void *base, uint64_t d0, uint64_t d1, uint64_t d2,
-                             uint64_t stride1_bytes, uint64_t stride2_bytes, uint32_t b0, uint32_t b1) {
+                             uint64_t stride1_bytes, uint64_t stride2_bytes, uint32_t b0, uint32_t b1,
+                             int dtype = DAG_BF16) {
   const cuuint64_t dims[3] = {d0, d1, d2};
   const cuuint64_t strides[2] = {stride1_bytes, stride2_bytes};
   const cuuint32_t box[3] = {b0, b1, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = p_encode_tiled(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box,
+  CUresult r = p_encode_tiled(m, dtype == DAG_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                              3, const_cast<void *>(base), dims, strides, box,
                               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(DAG_EUNSUPPORTED, "cuTensorMapEncodeTiled failed (%d)", (int)r);
@@ -858,6 +880,36 @@ static dag_status encode_out_map(CUtensorMap *m, const void *base, int dtype, ui
                               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(DAG_EUNSUPPORTED, "cuTensorMapEncodeTiled (output) failed (%d)", (int)r);
+  return DAG_OK;
+}
+
+// Tensor maps of a tensor-core GEMM node (bf16, or f32 split into tf32):
+// A box {K block, 128 rows}; B K-major box {K block, BN}, MN-major boxes of
+// 128 bytes of columns x K block; all with the 128-byte swizzle.  Plus the
+// output map of the TMA-store epilogue when C is 16-byte aligned.
+static dag_status gemm_maps(const Plan &P, int v, NodeParams &q, std::vector<CUtensorMap> &maps) {
+  const dag_node_desc &n = P.g.nodes[v];
+  if (n.op != DAG_OP_GEMM || (q.a_dt != DAG_BF16 && !P.tf32[v])) return DAG_OK;
+  if (((uintptr_t)q.A % 16) || ((uintptr_t)q.B % 16))
+    return fail(DAG_EUNSUPPORTED, "node %d: tensor-core GEMM operand view not 16-byte aligned", v);
+  const int M = q.M, N = q.N, K = q.K, B = n.batch;
+  const int dt = q.a_dt, es = esize(dt);
+  const uint32_t kb = dt == DAG_BF16 ? kBK : kBKF;          // 128 bytes of K
+  const uint32_t bn = dt == DAG_BF16 ? P.cfg[v] : kTf32BN;
+  CUtensorMap ma, mb;
+  dag_status s;
+  if ((s = encode_map(&ma, q.A, K, M, B, q.lda * es, (uint64_t)M * q.lda * es, kb, kBM, dt))) return s;
+  if (n.trans_b) s = encode_map(&mb, q.B, K, N, B, q.ldb * es, (uint64_t)N * q.ldb * es, kb, bn, dt);
+  else s = encode_map(&mb, q.B, N, K, B, q.ldb * es, (uint64_t)K * q.ldb * es, 128 / es, kb, dt);
+  if (s) return s;
+  q.tmap_a = (int)maps.size(); maps.push_back(ma);
+  q.tmap_b = (int)maps.size(); maps.push_back(mb);
+  q.tmap_c = -1;
+  if ((uintptr_t)q.C % 16 == 0) {
+    CUtensorMap mc;
+    if ((s = encode_out_map(&mc, q.C, q.c_dt, N, M, B, q.ldc))) return s;
+    q.tmap_c = (int)maps.size(); maps.push_back(mc);
+  }
   return DAG_OK;
 }
 
@@ -929,26 +981,7 @@ static dag_status create_impl(const dag_node_desc *nodes, int n_nodes, const dag
     for (int i = 0; i < k; ++i) vec &= ((size_t)g.coff[in[i]] * esize(g.bufs[in[i]].dtype)) % 16 == 0;
     vec &= ((size_t)g.coff[n.out] * esize(g.bufs[n.out].dtype)) % 16 == 0;
     q.vec = vec ? 1 : 0;
-    if (n.op == DAG_OP_GEMM && q.a_dt == DAG_BF16) {
-      if (((uintptr_t)q.A % 16) || ((uintptr_t)q.B % 16)) {
-        free_handle(h);
-        return fail(DAG_EUNSUPPORTED, "node %d: bf16 GEMM operand view not 16-byte aligned", v);
-      }
-      const int M = q.M, N = q.N, K = q.K, B = n.batch;
-      CUtensorMap ma, mb;
-      if ((s = encode_map(&ma, q.A, K, M, B, q.lda * 2, (uint64_t)M * q.lda * 2, kBK, kBM))) { free_handle(h); return s; }
-      if (n.trans_b) s = encode_map(&mb, q.B, K, N, B, q.ldb * 2, (uint64_t)N * q.ldb * 2, kBK, P.cfg[v]);
-      else s = encode_map(&mb, q.B, N, K, B, q.ldb * 2, (uint64_t)K * q.ldb * 2, 64, kBK);
-      if (s) { free_handle(h); return s; }
-      q.tmap_a = (int)maps.size(); maps.push_back(ma);
-      q.tmap_b = (int)maps.size(); maps.push_back(mb);
-      q.tmap_c = -1;
-      if ((uintptr_t)q.C % 16 == 0) {
-        CUtensorMap mc;
-        if ((s = encode_out_map(&mc, q.C, q.c_dt, N, M, B, q.ldc))) { free_handle(h); return s; }
-        q.tmap_c = (int)maps.size(); maps.push_back(mc);
-      }
-    }
+    if ((s = gemm_maps(P, v, q, maps))) { free_handle(h); return s; }
   }
 
   // ---- plan arrays in one device block ----
@@ -1457,24 +1490,7 @@ dag_status dagx::plan_into_region(const dag_node_desc *nodes, int n_nodes, const
     for (int i = 0; i < k; ++i) vec &= ((uintptr_t)dptr[in[i]] % 16) == 0;
     vec &= ((uintptr_t)dptr[n.out] % 16) == 0;
     q.vec = vec ? 1 : 0;
-    if (n.op == DAG_OP_GEMM && q.a_dt == DAG_BF16) {
-      if (((uintptr_t)q.A % 16) || ((uintptr_t)q.B % 16))
-        return fail(DAG_EUNSUPPORTED, "node %d: bf16 GEMM operand view not 16-byte aligned", v);
-      const int M = q.M, N = q.N, K = q.K, B = n.batch;
-      CUtensorMap ma, mb;
-      if ((s = encode_map(&ma, q.A, K, M, B, q.lda * 2, (uint64_t)M * q.lda * 2, kBK, kBM))) return s;
-      if (n.trans_b) s = encode_map(&mb, q.B, K, N, B, q.ldb * 2, (uint64_t)N * q.ldb * 2, kBK, P.cfg[v]);
-      else s = encode_map(&mb, q.B, N, K, B, q.ldb * 2, (uint64_t)K * q.ldb * 2, 64, kBK);
-      if (s) return s;
-      q.tmap_a = (int)maps.size(); maps.push_back(ma);
-      q.tmap_b = (int)maps.size(); maps.push_back(mb);
-      q.tmap_c = -1;
-      if ((uintptr_t)q.C % 16 == 0) {
-        CUtensorMap mc;
-        if ((s = encode_out_map(&mc, q.C, q.c_dt, N, M, B, q.ldc))) return s;
-        q.tmap_c = (int)maps.size(); maps.push_back(mc);
-      }
-    }
+    if ((s = gemm_maps(P, v, q, maps))) return s;
   }
   // layout inside the region; counters, flags and control block start at zero
   size_t o_maps = 0;

@@ -37,11 +37,8 @@ static_assert(kSmemBytes <= 232448, "shared memory budget");
 struct WorkerShared {
   int32_t tile;
   int32_t ok;
+  int32_t stage_ok;  // f32 tensor-core tiles: the next stage arrived
 };
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
 
 __device__ __forceinline__ void record_error(const ExecParams &p, uint32_t code, int tile) {
   if (atomicCAS(&p.ctrl->err_code, 0u, code) == 0u) p.ctrl->err_tile = (uint32_t)tile;
@@ -126,8 +123,11 @@ __device__ __forceinline__ void run_scheduler(const ExecParams &p, uint8_t *smem
     mbar_arrive(&ctl->slot_full[slot.idx]);
     slot.next(kSlots);
     if (t < 0) return;
-    if (td.op == T_GEMM_BF16) {
-      if (!gemm_produce(p, td, p.nodes[td.node], smem, ctl, st, globaltimer() + p.timeout_ns)) {
+    if (td.op == T_GEMM_BF16 || td.op == T_GEMM_TF32) {
+      const uint64_t dl = globaltimer() + p.timeout_ns;
+      const bool ok = td.op == T_GEMM_BF16 ? gemm_produce(p, td, p.nodes[td.node], smem, ctl, st, dl)
+                                           : tf32_produce(p, td, p.nodes[td.node], smem, ctl, st, dl);
+      if (!ok) {
         record_error(p, E_PIPE_TIMEOUT, t);
         ctl->fail = 1;
       }
@@ -142,6 +142,8 @@ __device__ __forceinline__ void run_scheduler(const ExecParams &p, uint8_t *smem
 __device__ __forceinline__ void run_mma(const ExecParams &p, uint8_t *smem, SmemCtl *ctl) {
   Ring slot = {0u, 0u}, st = {0u, 0u};
   uint32_t accb = 0, ph[2] = {0u, 0u};
+  uint32_t split_par = 0;  // bit s: parity of the next split[s] phase
+  uint32_t pq = 0;         // f32 K-block partials issued
   const uint64_t slot_limit = 2 * p.timeout_ns + 1000000000ull;
   for (;;) {
     if (!mbar_wait(&ctl->slot_full[slot.idx], slot.phase, globaltimer() + slot_limit)) {
@@ -153,17 +155,20 @@ __device__ __forceinline__ void run_mma(const ExecParams &p, uint8_t *smem, Smem
     slot.next(kSlots);
     if (t < 0) return;
     const TileDesc td = p.tiles[t];
-    if (td.op != T_GEMM_BF16) continue;
+    if (td.op != T_GEMM_BF16 && td.op != T_GEMM_TF32) continue;
     const uint64_t dl = globaltimer() + p.timeout_ns;
     if (!mbar_wait(&ctl->acc_empty[accb], ph[accb] ^ 1u, dl)) { ctl->fail = 1; return; }
     ph[accb] ^= 1u;
     tc_fence_after();
     if (p.trace_on) p.trace[t].stamp[S_MMA0] = globaltimer();
-    if (!gemm_mma(td, p.nodes[td.node], smem, ctl, st, ctl->tmem_base + accb * kAccCols, dl)) {
+    const uint32_t acc = ctl->tmem_base + accb * kAccCols;
+    const bool ok = td.op == T_GEMM_BF16 ? gemm_mma(td, p.nodes[td.node], smem, ctl, st, acc, dl)
+                                         : tf32_mma(p.nodes[td.node], smem, ctl, st, split_par, pq, acc, dl);
+    if (!ok) {
       ctl->fail = 1;
       return;
     }
-    mma_commit(&ctl->acc_full[accb]);
+    if (td.op == T_GEMM_BF16) mma_commit(&ctl->acc_full[accb]);  // f32 tiles signal per K block
     if (p.trace_on) p.trace[t].stamp[S_MMA1] = globaltimer();
     accb ^= 1u;
   }
@@ -177,12 +182,14 @@ __device__ __forceinline__ void run_workers(const ExecParams &p, uint8_t *smem, 
   const int wt = threadIdx.x - kWorkerBase;
   Ring slot = {0u, 0u};
   uint32_t accb = 0, ph[2] = {0u, 0u};
+  Tf32State fs = {{0u, 0u}, 0u, 0u};  // the workers split f32 stages and add up their partials
   float *fsm = reinterpret_cast<float *>(smem + kSmemStages);
   const uint64_t slot_limit = 2 * p.timeout_ns + 1000000000ull;
   for (;;) {
     if (wt == 0) {
       const bool ok = mbar_wait(&ctl->slot_full[slot.idx], slot.phase, globaltimer() + slot_limit);
       ws->tile = ok ? ctl->slot[slot.idx].t : -2;
+      ws->ok = 1;
     }
     worker_sync();
     const int t = ws->tile;
@@ -196,14 +203,27 @@ __device__ __forceinline__ void run_workers(const ExecParams &p, uint8_t *smem, 
     const NodeParams &np = p.nodes[td.node];
     bool ok = true;
     switch (td.op) {
-      case T_GEMM_BF16: {
+      case T_GEMM_BF16:
+      case T_GEMM_TF32: {
         stage_bias(td, np, ctl);
-        if (wt == 0) {
-          ws->ok = mbar_wait(&ctl->acc_full[accb], ph[accb], globaltimer() + p.timeout_ns) ? 1 : 0;
-          if (p.trace_on) p.trace[t].stamp[S_ACC] = globaltimer();
+        const uint32_t acc = ctl->tmem_base + accb * kAccCols;
+        if (td.op == T_GEMM_TF32) {
+          const bool mine = tf32_worker_loop(np, smem, ctl, fs, acc, &ws->stage_ok, globaltimer() + p.timeout_ns);
+          if (!mine) ws->ok = 0;  // any warp that timed out fails the tile
+          worker_sync();
+          if (p.trace_on && wt == 0) p.trace[t].stamp[S_ACC] = globaltimer();
+        } else {
+          for (int kb = 0; kb < (np.K + kBK - 1) / kBK; ++kb) {  // the MMA issuer consumes these stages
+            fs.st.next(kStages);
+            if (fs.st.idx == 0) ++fs.pass;
+          }
+          if (wt == 0) {
+            ws->ok = mbar_wait(&ctl->acc_full[accb], ph[accb], globaltimer() + p.timeout_ns) ? 1 : 0;
+            if (p.trace_on) p.trace[t].stamp[S_ACC] = globaltimer();
+          }
+          worker_sync();
+          ph[accb] ^= 1u;
         }
-        worker_sync();
-        ph[accb] ^= 1u;
         ok = ws->ok != 0;
         if (ok) {
           tc_fence_after();
@@ -227,9 +247,10 @@ __device__ __forceinline__ void run_workers(const ExecParams &p, uint8_t *smem, 
     worker_sync();
     if (wt == 0) {
       if (p.trace_on) p.trace[t].stamp[S_SYNC] = globaltimer();
-      if (td.op == T_GEMM_BF16) mbar_arrive(&ctl->acc_empty[accb]);
+      const bool tc = td.op == T_GEMM_BF16 || td.op == T_GEMM_TF32;
+      if (tc) mbar_arrive(&ctl->acc_empty[accb]);
       if (!ok) {
-        record_error(p, td.op == T_GEMM_BF16 ? E_PIPE_TIMEOUT : E_BAD_TILE, t);
+        record_error(p, tc ? E_PIPE_TIMEOUT : E_BAD_TILE, t);
         ctl->fail = 1;
       } else {
         __threadfence();
@@ -247,7 +268,7 @@ __device__ __forceinline__ void run_workers(const ExecParams &p, uint8_t *smem, 
       }
       mbar_arrive(&ctl->slot_empty[slot.idx]);
     }
-    if (td.op == T_GEMM_BF16) accb ^= 1u;
+    if (td.op == T_GEMM_BF16 || td.op == T_GEMM_TF32) accb ^= 1u;
     slot.next(kSlots);
   }
 }
@@ -263,10 +284,16 @@ __global__ void __launch_bounds__(kThreads, 1) dag_exec_kernel(const __grid_cons
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&ctl->full[s], 1);
       mbar_init(&ctl->empty[s], 1);
+      mbar_init(&ctl->split[s], 1);
+      ctl->issued[s] = 0;
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&ctl->acc_full[b], 1);
       mbar_init(&ctl->acc_empty[b], 1);
+    }
+    for (int q = 0; q < kParts; ++q) {
+      mbar_init(&ctl->pfull[q], 1);
+      mbar_init(&ctl->pempty[q], kWorkers / 32);
     }
     for (int s = 0; s < kSlots; ++s) {
       mbar_init(&ctl->slot_full[s], 1);

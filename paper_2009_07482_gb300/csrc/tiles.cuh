@@ -54,6 +54,10 @@ struct TileSlot {
 struct SmemCtl {
   uint64_t full[kStages];      // TMA -> MMA: stage filled
   uint64_t empty[kStages];     // MMA -> TMA: stage consumed
+  uint64_t split[kStages];     // workers -> MMA: f32 stage split into tf32 halves
+  uint32_t issued[kStages];    // producer: uses of stage s whose loads were issued
+  uint64_t pfull[kParts];      // MMA -> workers: f32 K-block partial p in TMEM
+  uint64_t pempty[kParts];     // workers (8 warps) -> MMA: partial p added up
   uint64_t acc_full[2];        // MMA -> workers: accumulator b complete
   uint64_t acc_empty[2];       // workers -> MMA: accumulator b drained
   uint64_t slot_full[kSlots];  // scheduler -> MMA, workers: slot published
@@ -71,6 +75,24 @@ struct Ring {
     if (++idx == n) { idx = 0; phase ^= 1u; }
   }
 };
+
+// The splitters skip the stages of bf16 tiles without waiting on them, so
+// for an f32 stage a parity wait alone could match an older phase of full[s].
+// They first wait until the producer has issued that use of the stage (then
+// every earlier phase of full[s] has completed, and the next one cannot
+// complete before they split this one), then wait on its parity.
+__device__ __forceinline__ void stage_issued(SmemCtl *ctl, uint32_t s) {
+  volatile uint32_t *c = &ctl->issued[s];
+  *c = *c + 1u;
+}
+__device__ __forceinline__ bool stage_wait_use(SmemCtl *ctl, uint32_t s, uint32_t use, uint64_t deadline) {
+  const volatile uint32_t *c = &ctl->issued[s];
+  uint32_t n = 0;
+  while ((int32_t)(*c - (use + 1u)) < 0) {
+    if ((++n & 255u) == 0 && globaltimer() > deadline) return false;
+  }
+  return mbar_wait(&ctl->full[s], use & 1u, deadline);
+}
 
 // ---------------------------------------------------------------------------
 // bf16 GEMM tile, 128 x BN on the tensor cores (tcgen05, f32 accumulator in
@@ -101,6 +123,7 @@ __device__ __forceinline__ bool gemm_produce(const ExecParams &p, const TileDesc
     } else {
       for (int j = 0; j < BN / 64; ++j) tma_load_3d(dB + j * (64 * kBK * 2), tb, bar, n0 + j * 64, kb * kBK, bt);
     }
+    stage_issued(ctl, st.idx);
     st.next(kStages);
   }
   return true;
@@ -135,6 +158,250 @@ __device__ __forceinline__ bool gemm_mma(const TileDesc &t, const NodeParams &np
     st.next(kStages);
   }
   return true;
+}
+
+// ---------------------------------------------------------------------------
+// f32 GEMM tile, 128 x 64, on the tensor cores with the 3 x TF32 split: each
+// operand x = hi + lo with hi = tf32(x), lo = tf32(x - hi), and
+// A.B ~= Ahi.Bhi + Ahi.Blo + Alo.Bhi (the dropped Alo.Blo and the rounding of
+// lo are ~2^-22 relative), accumulated in f32 in TMEM.  One stage holds one
+// K block of 32 (128-byte rows):
+//   A area (16 KiB): A, K-major; split in place into Ahi
+//   B area: [0, 8K) B (K-major after the split; Bhi), [8K, 16K) Blo,
+//           [16K, 32K) Alo
+// The producer loads raw f32 with TMA; the workers round in place, transpose
+// an MN-major B into K-major, and signal split[s]; the MMA issuer then runs
+// three tf32 MMAs per K step of 8.
+// ---------------------------------------------------------------------------
+constexpr int kTf32BBytes = kTf32BN * kBKF * 4;  // 8 KiB
+constexpr int kTf32Blo = kTf32BBytes;            // offsets in the B area
+constexpr int kTf32Alo = 2 * kTf32BBytes;
+static_assert(kTf32Alo + kStageA <= kStageB, "tf32 stage layout");
+
+__device__ __forceinline__ bool tf32_produce(const ExecParams &p, const TileDesc &t, const NodeParams &np,
+                                             uint8_t *smem, SmemCtl *ctl, Ring &st, uint64_t deadline) {
+  const int M = np.M;
+  const int bt = t.r0 / M, m0 = t.r0 - bt * M, n0 = t.c0;
+  const int kiters = (np.K + kBKF - 1) / kBKF;
+  const CUtensorMap *ta = p.tmaps + np.tmap_a;
+  const CUtensorMap *tb = p.tmaps + np.tmap_b;
+  const int trans_b = np.trans_b;
+  uint8_t *sA = smem;
+  uint8_t *sB = smem + kStages * kStageA;
+  for (int kb = 0; kb < kiters; ++kb) {
+    if (!mbar_wait(&ctl->empty[st.idx], st.phase ^ 1u, deadline)) return false;
+    uint64_t *bar = &ctl->full[st.idx];
+    mbar_arrive_expect_tx(bar, (uint32_t)(kStageA + kTf32BBytes));
+    tma_load_3d(sA + st.idx * kStageA, ta, bar, kb * kBKF, m0, bt);
+    uint8_t *dB = sB + st.idx * kStageB;
+    if (trans_b) {
+      tma_load_3d(dB, tb, bar, kb * kBKF, n0, bt);  // box {32 (K), 64 (N)}
+    } else {
+      // box {32 (N), 32 (K)}: 4 KiB per 32 columns
+      for (int j = 0; j < kTf32BN / 32; ++j) tma_load_3d(dB + j * 4096, tb, bar, n0 + j * 32, kb * kBKF, bt);
+    }
+    stage_issued(ctl, st.idx);
+    st.next(kStages);
+  }
+  return true;
+}
+
+// tf32 rounding of an f32 bit pattern: round to nearest, ties away from zero,
+// on the 13 dropped mantissa bits (the value's low 13 bits become zero, so
+// the tensor cores read it exactly)
+__device__ __forceinline__ uint32_t tf32_bits(uint32_t u) { return (u + 0x1000u) & 0xFFFFE000u; }
+
+// hi/lo split of 4 consecutive f32 (one 16-byte chunk)
+__device__ __forceinline__ void split1(uint32_t x, uint32_t &hi, uint32_t &lo) {
+  hi = tf32_bits(x);
+  lo = tf32_bits(__float_as_uint(__uint_as_float(x) - __uint_as_float(hi)));
+}
+__device__ __forceinline__ void split4(uint4 x, uint4 &hi, uint4 &lo) {
+  split1(x.x, hi.x, lo.x);
+  split1(x.y, hi.y, lo.y);
+  split1(x.z, hi.z, lo.z);
+  split1(x.w, hi.w, lo.w);
+}
+
+// Split one filled stage (the 256 workers, wt = 0..255).  A and a K-major B:
+// element-wise, hi in place and lo at the same layout offset.  An MN-major B
+// is transposed in place: box j holds columns 32j..32j+31 as 32 K rows of 128
+// bytes, chunk c of row k at (c ^ (k % 8)); threads 0..127 each read one
+// 4 (K) x 4 (N) block, all workers sync, then each writes its block K-major
+// (row n, chunk k/4 at ((k/4) ^ (n % 8))).
+__device__ __forceinline__ void tf32_split_stage(uint8_t *a, uint8_t *b, int trans_b, int wt) {
+  constexpr int kA = kStageA / 16 / kWorkers;       // 4 chunks of A per thread
+  constexpr int kB = kTf32BBytes / 16 / kWorkers;   // 2 chunks of B per thread
+  uint4 *A4 = reinterpret_cast<uint4 *>(a);
+  uint4 *Alo = reinterpret_cast<uint4 *>(b + kTf32Alo);
+  uint4 *B4 = reinterpret_cast<uint4 *>(b);
+  uint4 *Blo = reinterpret_cast<uint4 *>(b + kTf32Blo);
+  uint4 xa[kA], xb[kB];
+#pragma unroll
+  for (int j = 0; j < kA; ++j) xa[j] = A4[wt + j * kWorkers];
+  if (trans_b) {
+#pragma unroll
+    for (int j = 0; j < kB; ++j) xb[j] = B4[wt + j * kWorkers];
+  }
+#pragma unroll
+  for (int j = 0; j < kA; ++j) {
+    uint4 hi, lo;
+    split4(xa[j], hi, lo);
+    A4[wt + j * kWorkers] = hi;
+    Alo[wt + j * kWorkers] = lo;
+  }
+  if (trans_b) {
+#pragma unroll
+    for (int j = 0; j < kB; ++j) {
+      uint4 hi, lo;
+      split4(xb[j], hi, lo);
+      B4[wt + j * kWorkers] = hi;
+      Blo[wt + j * kWorkers] = lo;
+    }
+    return;
+  }
+  const bool mine = wt < 128;  // 8 K quads x 16 N quads
+  const int kq = wt & 7, nq = (wt >> 3) & 15;
+  uint4 v[4];
+  if (mine) {
+    const int j = nq >> 3, c = nq & 7;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int k = 4 * kq + r;
+      v[r] = B4[(j * 4096 + k * 128 + ((c ^ (k & 7)) << 4)) >> 4];
+    }
+  }
+  worker_sync();  // every block read before any is overwritten
+  if (mine) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int n = 4 * nq + q;
+      uint4 col;
+      col.x = q == 0 ? v[0].x : q == 1 ? v[0].y : q == 2 ? v[0].z : v[0].w;
+      col.y = q == 0 ? v[1].x : q == 1 ? v[1].y : q == 2 ? v[1].z : v[1].w;
+      col.z = q == 0 ? v[2].x : q == 1 ? v[2].y : q == 2 ? v[2].z : v[2].w;
+      col.w = q == 0 ? v[3].x : q == 1 ? v[3].y : q == 2 ? v[3].z : v[3].w;
+      uint4 hi, lo;
+      split4(col, hi, lo);
+      const int o = (n * 128 + ((kq ^ (n & 7)) << 4)) >> 4;
+      B4[o] = hi;
+      Blo[o] = lo;
+    }
+  }
+}
+
+// MMA side of an f32 tile: three tf32 MMAs per K step of 8 (32 bytes).  The
+// tensor cores' f32 accumulation is not round-to-nearest, and its error
+// grows with the number of MMAs summed into one accumulator; so each K block
+// goes into a fresh 64-column partial (a ring of kParts in the tile's TMEM
+// accumulator), and the workers add the partials in f32 registers.  Partial
+// q of the CTA's stream of f32 K blocks is slot q % kParts, parity
+// (q / kParts) & 1.
+__device__ __forceinline__ bool tf32_mma(const NodeParams &np, uint8_t *smem, SmemCtl *ctl, Ring &st,
+                                         uint32_t &split_par, uint32_t &pq, uint32_t tmem_acc, uint64_t deadline) {
+  const int kiters = (np.K + kBKF - 1) / kBKF;
+  constexpr uint32_t idesc = idesc_tf32((uint32_t)kTf32BN);
+  uint8_t *sA = smem;
+  uint8_t *sB = smem + kStages * kStageA;
+  for (int kb = 0; kb < kiters; ++kb) {
+    if (!mbar_wait(&ctl->split[st.idx], (split_par >> st.idx) & 1u, deadline)) return false;
+    split_par ^= 1u << st.idx;
+    const uint32_t ps = pq % kParts;
+    if (!mbar_wait(&ctl->pempty[ps], ((pq / kParts) & 1u) ^ 1u, deadline)) return false;
+    const uint32_t tmem_d = tmem_acc + ps * kTf32BN;
+    tc_fence_after();
+    const uint32_t ahi = smem_u32(sA + st.idx * kStageA);
+    const uint32_t bhi = smem_u32(sB + st.idx * kStageB);
+    const uint32_t blo = bhi + kTf32Blo, alo = bhi + kTf32Alo;
+#pragma unroll
+    for (int kk = 0; kk < kBKF / 8; ++kk) {
+      const uint64_t dah = smem_desc_sw128(ahi + kk * 32, 16, 1024);
+      const uint64_t dal = smem_desc_sw128(alo + kk * 32, 16, 1024);
+      const uint64_t dbh = smem_desc_sw128(bhi + kk * 32, 16, 1024);
+      const uint64_t dbl = smem_desc_sw128(blo + kk * 32, 16, 1024);
+      // the small products first, then the large one
+      mma_tf32(tmem_d, dal, dbh, idesc, kk != 0 ? 1u : 0u);
+      mma_tf32(tmem_d, dah, dbl, idesc, 1u);
+      mma_tf32(tmem_d, dah, dbh, idesc, 1u);
+    }
+    mma_commit(&ctl->empty[st.idx]);
+    mma_commit(&ctl->pfull[ps]);
+    ++pq;
+    st.next(kStages);
+  }
+  return true;
+}
+
+// Worker side of an f32 tile: for each K block, split its stage (then the
+// MMA issuer may run it) and add up the partial of the K block kLag earlier
+// (each warp: its TMEM lane quadrant, columns half*32 .. +32 of the 64); at
+// the end the sum goes to columns 0..63 of the accumulator for the epilogue.
+// Waits are taken by the leader (wt == 0) or a warp's lane 0 and shared, so
+// all workers reach the same barriers; false if any wait ran out.
+constexpr int kLag = 2;
+static_assert(kLag < kParts, "the MMA issuer runs up to kParts partials ahead");
+
+struct Tf32State {
+  Ring st;          // position in the stage ring
+  uint32_t pass;    // completed passes over the stage ring
+  uint32_t pq;      // f32 K-block partials added up
+};
+
+__device__ __forceinline__ bool tf32_worker_loop(const NodeParams &np, uint8_t *smem, SmemCtl *ctl, Tf32State &fs,
+                                                 uint32_t tmem_acc, volatile int32_t *shared_ok, uint64_t deadline) {
+  const int wt = threadIdx.x - kWorkerBase;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int half = (wt >> 5) >> 2;
+  const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+  const int kiters = (np.K + kBKF - 1) / kBKF;
+  const int trans_b = np.trans_b;
+  uint8_t *sA = smem;
+  uint8_t *sB = smem + kStages * kStageA;
+  float sum[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) sum[i] = 0.0f;
+  bool ok = true, drain_ok = true;
+  for (int kb = 0; kb < kiters + kLag; ++kb) {
+    if (kb < kiters) {
+      if (wt == 0) *shared_ok = ok && stage_wait_use(ctl, fs.st.idx, fs.pass, deadline) ? 1 : 0;
+      worker_sync();
+      ok = *shared_ok != 0;
+      if (ok) {
+        tf32_split_stage(sA + fs.st.idx * kStageA, sB + fs.st.idx * kStageB, trans_b, wt);
+        fence_proxy_async_shared();  // generic writes -> visible to the tensor cores
+      } else if (!trans_b) {
+        worker_sync();  // the split's own barrier
+      }
+      worker_sync();
+      if (wt == 0 && ok) mbar_arrive(&ctl->split[fs.st.idx]);
+      fs.st.next(kStages);
+      if (fs.st.idx == 0) ++fs.pass;
+    }
+    if (kb >= kLag) {
+      const uint32_t ps = fs.pq % kParts;
+      if (drain_ok) {
+        int w = 0;
+        if (lane == 0) w = mbar_wait(&ctl->pfull[ps], (fs.pq / kParts) & 1u, deadline) ? 1 : 0;
+        drain_ok = __shfl_sync(0xffffffffu, w, 0) != 0;
+      }
+      if (drain_ok) {
+        tc_fence_after();
+        float v[32];
+        tmem_ld32(tmem_acc + lanes + ps * kTf32BN + half * 32, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) sum[i] += v[i];
+        tc_fence_before();
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ctl->pempty[ps]);
+      ++fs.pq;
+    }
+  }
+  if (ok && drain_ok) {
+    tmem_st32(tmem_acc + lanes + half * 32, sum);
+    tc_fence_before();
+  }
+  return ok && drain_ok;
 }
 
 // Epilogue (workers): TMEM accumulator -> scale, bias, activation, cast ->

@@ -181,3 +181,37 @@ def test_plan_algorithmic_totals():
     assert info.flops == pytest.approx(sum(w.node_flops(k) for k, x in enumerate(w.nodes) if x.op == "gemm"))
     assert info.flops == pytest.approx(64.42450944e9)
     assert info.bytes == pytest.approx(sum(w.node_bytes(k) for k in range(len(w.nodes))))
+
+
+def _f32_gemm_with_views(a_off):
+    """An f32 GEMM whose A is a column slice starting at column a_off of a
+    wider buffer, and a second GEMM on a plain buffer."""
+    w = Workload("f32_views")
+    P = w.buf(256, 96 + 8, F32, "input", ("uniform", 1))
+    A = w.buf(256, 96, F32, "inter", view_of=P, col_offset=a_off)
+    B = w.buf(96, 200, F32, "input", ("uniform", 2))
+    C = w.buf(256, 200, F32, "output")
+    w.node("gemm", A, C, b=B)
+    X = w.buf(300, 64, F32, "input", ("uniform", 3))
+    D = w.buf(300, 200, F32, "output")
+    w.node("gemm", X, D, b=w.buf(64, 200, F32, "input", ("uniform", 4)))
+    return w
+
+
+@pytest.mark.parametrize("a_off,mode", [(0, 0), (4, 0), (1, 0), (0, 1)])
+def test_f32_gemm_tile_kind(a_off, mode):
+    """f32 GEMMs take the tensor-core 3 x TF32 tiles (128 x 64) unless an
+    operand view does not start on a 16-byte boundary or SIMT is asked for;
+    then the SIMT FFMA shapes (64/128 rows x 64/128 columns)."""
+    w = _f32_gemm_with_views(a_off)
+    n, e, b = dagmod.describe(w, resident_inputs=True)
+    t, _ = abi.dag_plan_host(n, e, b, dagmod.options(f32_gemm=mode), 148)
+    for node, want_tc in ((0, mode == 0 and a_off % 4 == 0), (1, mode == 0)):
+        mine = t[t[:, 0] == node]
+        rows = mine[:, 2] - mine[:, 1]
+        cols = mine[:, 4] - mine[:, 3]
+        if want_tc:
+            assert (mine[:, 5] == 64).all()
+            assert rows.max() == 128 and cols.max() == 64
+        else:
+            assert set(mine[:, 5].tolist()) <= {0, 1, 2}

@@ -81,6 +81,68 @@ def test_gemm(case):
     _roundtrip(_gemm_case(**case))
 
 
+@pytest.mark.parametrize("case", [c for c in GEMM_CASES if c["dt"] == F32],
+                         ids=lambda c: "-".join(f"{k}{v}" for k, v in c.items()))
+def test_gemm_f32_simt(case):
+    """The same f32 cases on the SM cores (exact-f32 FFMA tiles)."""
+    _roundtrip(_gemm_case(**case), options(trace=1, f32_gemm=abi.DAG_F32_GEMM_SIMT))
+
+
+TF32_CASES = [
+    dict(M=128, N=64, K=32, dt=F32),                          # one tile, one stage
+    dict(M=384, N=640, K=4096, dt=F32, act="relu"),           # long K: the stage ring wraps many times
+    dict(M=257, N=65, K=33, dt=F32, trans_b=1),               # ragged in every dimension
+    dict(M=200, N=300, K=1000, dt=F32, out_dt=BF16, act="gelu", scale=0.25),
+    dict(M=64, N=96, K=160, dt=F32, batch=5),                 # batched, M below one tile
+    dict(M=96, N=128, K=96, dt=F32, batch=2, trans_b=1, bias=False),
+]
+
+
+@pytest.mark.parametrize("case", TF32_CASES, ids=lambda c: "-".join(f"{k}{v}" for k, v in c.items()))
+def test_gemm_f32_tensor_cores(case):
+    """3 x TF32 tiles within the f32 tolerance (a one-term tf32 product would
+    miss it by about two orders of magnitude), in both B layouts."""
+    w = _gemm_case(**case)
+    d = Dag(w, options())
+    assert (d.tiles()[:, 5] == 64).all()  # planned as tensor-core f32 tiles
+    d.close()
+    _roundtrip(w)
+
+
+def test_f32_unaligned_view_runs_on_simt_tiles():
+    w = Workload("f32_view")
+    P = w.buf(256, 100, F32, "input", ("uniform", 1))
+    A = w.buf(256, 96, F32, "inter", view_of=P, col_offset=1)   # 4-byte offset: no TMA
+    C = w.buf(256, 200, F32, "output")
+    w.node("gemm", A, C, b=w.buf(96, 200, F32, "input", ("uniform", 2)))
+    d = Dag(w, options())
+    assert set(d.tiles()[:, 5].tolist()) <= {0, 1, 2}
+    d.close()
+    _roundtrip(w)
+
+
+def test_bf16_and_f32_gemms_interleaved_in_one_cta():
+    """One CTA runs bf16 and f32 tensor-core tiles alternately, so stages of
+    the ring change hands between the MMA issuer and the splitter warps."""
+    w = Workload("mixed")
+    xs = []
+    for i, dt in enumerate([BF16, F32, BF16, F32]):
+        A = w.buf(256, 192 + 64 * i, dt, "input", ("uniform", 10 + i))
+        B = w.buf(192 + 64 * i, 128, dt, "input", ("uniform", 20 + i))
+        C = w.buf(256, 128, F32, "inter")
+        w.node("gemm", A, C, b=B, act="relu")
+        xs.append(C)
+    S = w.buf(256, 128, F32, "inter")
+    w.node("add", xs[0], S, b=xs[1])
+    T = w.buf(256, 128, F32, "inter")
+    w.node("add", xs[2], T, b=xs[3])
+    U = w.buf(256, 128, F32, "output")
+    w.node("add", S, U, b=T)
+    for sched in (abi.DAG_SCHED_RANK_MODEL, abi.DAG_SCHED_FIFO):
+        _roundtrip(w, options(trace=1, max_ctas=1, scheduler=sched), coarse_too=False)
+    _roundtrip(w, options(trace=1))
+
+
 @pytest.mark.parametrize("bn", [64, 128, 256])
 @pytest.mark.parametrize("trans_b", [0, 1])
 @pytest.mark.parametrize("out_dt", [F32, BF16])
