@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mlp_bf16",
-                    choices=["mlp_bf16", "mlp_f32", "fork_join", "encoder", "batched", "serving"])
+                    choices=["mlp_bf16", "mlp_f32", "fork_join", "encoder", "heads", "batched", "serving", "exp1"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="batched: skip the cost-model comparison")
     ap.add_argument("--profile", action="store_true", help="few steps, no side measurements (for ncu)")
@@ -66,8 +66,81 @@ def make_workload(name):
         return branchy_mlp("f32"), "branchy MLP inference DAG, f32: batch 512, widths as mlp_bf16"
     if name == "fork_join":
         return fork_join(256), "fork-join DAG (paper Fig. 1): 3 GEMMs 256^3 f32 + add"
+    if name == "heads":
+        from synth.workloads import transformer_heads
+        return transformer_heads(16, 256), ("the paper's transformer-layer DAG (§6): 16 heads, beta = 256, f32; "
+                                            "per head 3 projections, Q.K^T, softmax, B.V, C.W_h")
     return encoder_block(), ("transformer encoder block DAG: 8 x 256 tokens, d_model 1024, 16 heads as fork "
                              "branches, out proj, FFN 4096 GELU; bf16 in / f32 accumulate")
+
+
+def paper_alg1(d, abi, reps=8):
+    """The paper's own form (Alg. 1 on CUDA streams, dag_submit_cq) on the
+    same DAG: the task components as given (the whole DAG when none are) with
+    q = 1..5 command queues, and eager (every kernel a component, one queue,
+    a host callback per kernel).  Median device makespans in us."""
+    import statistics
+    out = {"components_given": {}, "eager_us": None, "eager_gap_us": None}
+    for q in range(1, 6):
+        rs = [d.run_cq(n_queues=q, components=abi.DAG_TC_GIVEN) for _ in range(reps)]
+        out["components_given"][q] = statistics.median(r.device_us for r in rs)
+        out["n_components"] = rs[0].n_components
+    rs = [d.run_cq(n_queues=1, components=abi.DAG_TC_PER_KERNEL) for _ in range(reps)]
+    out["eager_us"] = statistics.median(r.device_us for r in rs)
+    out["eager_gap_us"] = statistics.median(r.gap_us for r in rs)
+    best_q = min(out["components_given"], key=out["components_given"].get)
+    out["best_q"] = best_q
+    out["best_us"] = out["components_given"][best_q]
+    out["speedup_best_q_over_q1"] = out["components_given"][1] / out["best_us"]
+    return out
+
+
+def run_exp1(args):
+    """The paper's Experiment 1 on this GPU: transformer DAGs with H heads at
+    beta = 256 (f32); per H the persistent executor, the kernel-by-kernel
+    path, and Alg. 1 on streams (clustering: one component per head,
+    q = 1..5; eager).  One JSON line."""
+    import statistics
+    import torch
+    from paper_2009_07482_gb300 import _binding as abi
+    from paper_2009_07482_gb300 import build as libbuild
+    from paper_2009_07482_gb300.dag import Dag, options
+    from synth.workloads import transformer_heads
+    libbuild.build()
+    stream = torch.cuda.current_stream()
+    rows = []
+    with ClockSampler(0) as clk:
+        for H in (1, 2, 4, 8, 16):
+            w = transformer_heads(H, 256)
+            d = Dag(w, options(), resident_inputs=True)
+            d.set_inputs(w.make_inputs(_INPUTS))
+
+            def timed(submit, n):
+                out = []
+                for i in range(n + 3):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    submit(stream.cuda_stream)
+                    b.record(stream)
+                    abi.check(d.wait(), "wait")
+                    if i >= 3:
+                        out.append(a.elapsed_time(b) * 1e3)
+                return statistics.median(out)
+
+            row = {"heads": H, "persistent_us": timed(d.submit, 30), "coarse_us": timed(d.submit_coarse, 10)}
+            row.update(paper_alg1(d, abi, reps=6))
+            row["speedup_persistent_over_best"] = row["best_us"] / row["persistent_us"]
+            rows.append(row)
+            d.close()
+    last = rows[-1]
+    line = {"metric": "DAG makespan (us), paper §6 Experiment 1 transformer DAGs (beta 256, f32)",
+            "value": last["persistent_us"], "unit": "us", "higher_is_better": False, "n_gpus": 1,
+            "dtype": "f32", "data": "synthetic (seeded SplitMix64)",
+            "config": {"workload": "transformer_heads H in {1,2,4,8,16}, beta 256; value = persistent executor at H=16",
+                       "f32_gemm": "tensor cores (3 x TF32 split)"},
+            "sweep": rows, "clocks": clk.summary()}
+    print(json.dumps(line))
+    return 0
 
 
 def dist_env():
@@ -121,6 +194,11 @@ def oracle_model(workload, ra=4, rb=12):
         w = fork_join(256)
         t = _oracle_seconds(w, w.make_inputs(), repeat=3)
         return t, "fork-join 256^3 f32: the whole DAG, mean of 3 runs", (w, 256, t, 0.0)
+    if workload == "heads":
+        from synth.workloads import transformer_heads
+        w = transformer_heads(1, 256)
+        t = _oracle_seconds(w, w.make_inputs(_INPUTS))
+        return 16 * t, f"transformer heads: 1 of 16 independent heads (7 kernels, {t:.2f} s), times 16", (w, 1, t, 0.0)
     if workload == "batched":
         from synth.workloads import random_batch
         ws = random_batch(256)
@@ -149,6 +227,10 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
+    if args.workload in ("serving", "exp1"):
+        print(json.dumps({"impl": "reference", "unavailable": f"--workload {args.workload} has no oracle arm; "
+                          "its DAGs are timed in the other workloads"}))
+        return 0
     _, desc = make_workload(args.workload)
     full, cal_desc, (w, rows, t_cal, slope) = oracle_model(args.workload)
     if args.workload.startswith("mlp"):
@@ -176,6 +258,8 @@ def run_reference(args):
             t = t + (scale_rows - rows) * slope
         elif args.workload == "encoder":
             t = 8 * t
+        elif args.workload == "heads":
+            t = 16 * t
         if i >= args.warmup:
             per.append(t)
     ms = statistics.mean(per) * 1e3
@@ -420,6 +504,8 @@ def main():
         return run_reference(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "exp1":
+        return run_exp1(args)
     import numpy as np
     import torch
 
@@ -500,6 +586,7 @@ def main():
         return 0
     coarse_us, _ = timed(d.submit_coarse, max(3, args.steps // 4) if batched else max(10, args.steps // 4), 3)
     n_coarse_launches = sum(1 for _ in w.nodes)
+    alg1 = None if batched else paper_alg1(d, abi, reps=8)
 
     # max over ranks of the mean step time
     mean_us = statistics.mean(fine_us)
@@ -597,6 +684,9 @@ def main():
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),
     }
+    if alg1:
+        alg1["speedup_persistent_over_best"] = alg1["best_us"] / med
+        line["paper_alg1"] = alg1
     if batched and not args.no_learned:
         def timed_fn(dd, n):
             out = []

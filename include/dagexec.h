@@ -82,14 +82,15 @@ typedef struct {
  * roles define E_I (buffer -> kernel) and E_O (kernel -> buffer).
  *   GEMM     out = act(scale * A.B + bias)  A: (batch*M) x K; B: (batch*K) x N,
  *            or (batch*N) x K with trans_b = 1; bias: 1 x N or -1;
- *            out: (batch*M) x N.  A and B share one dtype; f32 runs exact-f32
- *            SIMT tiles, bf16 runs tensor-core tiles with f32 accumulation.
+ *            out: (batch*M) x N.  A and B share one dtype; bf16 runs
+ *            tensor-core tiles with f32 accumulation, f32 runs as set by
+ *            dag_options.f32_gemm (dag_f32_gemm).
  *   ADD      out = act(A + B), same shapes.
  *   SOFTMAX  out[i,:] = softmax(scale * A[i,:]) (max-subtracted).
  *   UNARY    out = act(A).
  * component: task component id (paper §3, T in the partition of K); used by
- *   dag_analyze for FRONT/END/IN and intra/inter edge classification; on one
- *   GPU all components execute in the same persistent launch.
+ *   dag_analyze for FRONT/END/IN and intra/inter edge classification and by
+ *   dag_submit_cq; dag_submit runs all components in one persistent launch.
  */
 typedef struct {
   int32_t op;  /* dag_op */
@@ -199,6 +200,54 @@ dag_status dag_submit(dag_handle *h, void *stream);
  * one launch per kernel in topological order on `stream` (the same tile code,
  * a grid of that kernel's tiles, no cross-kernel overlap), then readbacks. */
 dag_status dag_submit_coarse(dag_handle *h, void *stream);
+
+/*
+ * dag_submit_cq: the paper's own fine-grained form (§5, Alg. 1) on CUDA
+ * streams, as a second, host-driven executor over the same tiles:
+ *   schedule: ready task components (every kernel of FRONT(T) has all its
+ *     predecessors finished) wait in a priority queue F ordered by the largest
+ *     bottom-level rank of their FRONT kernels (or by id with fifo = 1); the
+ *     GPU is the only device, so one component at a time holds it;
+ *   setup_cq: the kernels of T, starting from FRONT(T) and each once all its
+ *     predecessors in T are processed, go round-robin to n_queues CUDA streams
+ *     (the command queues Q): the uploads of its isolated inputs, then its
+ *     launch (a grid of the kernel's tiles, as in dag_submit_coarse), then the
+ *     readback of its output if registered; a predecessor on another stream
+ *     is waited on through its event (the set E_Q);
+ *   callbacks: after each kernel of END(T), a host function (the paper's cb)
+ *     marks it finished; when all of END(T) have, T is finished, its ready
+ *     successor components enter F and the device is returned.
+ * Synchronous: returns when every kernel and readback has completed.
+ * Components: DAG_TC_GIVEN uses dag_node_desc.component (the partition must
+ * leave the component graph acyclic, else DAG_ECYCLE); DAG_TC_WHOLE puts the
+ * DAG in one component; DAG_TC_PER_KERNEL makes every kernel a component
+ * (the coarse-grained policies of §6, Experiments 2-3: one callback per
+ * kernel).  Timings come from CUDA events on the streams; node_start_us /
+ * node_end_us, if not NULL, receive each kernel's [start, end) from the first
+ * dispatch (n_nodes entries each, caller-owned).
+ */
+typedef enum { DAG_TC_GIVEN = 0, DAG_TC_WHOLE = 1, DAG_TC_PER_KERNEL = 2 } dag_tc;
+
+typedef struct {
+  int32_t n_queues;       /* command queues (streams) per dispatched component, 1..32 */
+  int32_t components;     /* dag_tc */
+  int32_t fifo;           /* 1: F ordered by component id instead of rank */
+  int32_t pad;
+  uint64_t timeout_ns;    /* limit on waiting for any callback; 0 = 10 s; DAG_ETIMEOUT poisons the handle */
+  float *node_start_us;   /* optional [n_nodes] */
+  float *node_end_us;     /* optional [n_nodes] */
+} dag_cq_options;
+
+typedef struct {
+  double device_us;       /* first dispatch -> last kernel end, CUDA events */
+  double host_us;         /* the schedule loop's wall time, first dispatch -> last callback handled */
+  double gap_us;          /* summed device idle between one component's last kernel end and the
+                             next component's first kernel start (the callback round trip) */
+  int32_t n_components;
+  int32_t n_callbacks;
+} dag_cq_result;
+
+dag_status dag_submit_cq(dag_handle *h, const dag_cq_options *opts, dag_cq_result *result);
 
 /* dag_wait: block until the last submit finished or timeout_ns passed
  * (DAG_ETIMEOUT, the submit stays in flight).  Then reads the device error

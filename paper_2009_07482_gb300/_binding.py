@@ -27,6 +27,7 @@ DAG_ACT_NONE, DAG_ACT_RELU, DAG_ACT_GELU = 0, 1, 2
 DAG_BUF_INPUT, DAG_BUF_OUTPUT, DAG_BUF_RESIDENT = 1, 2, 4
 DAG_SCHED_RANK_MODEL, DAG_SCHED_RANK_GIVEN, DAG_SCHED_FIFO = 0, 1, 2
 DAG_F32_GEMM_TENSOR, DAG_F32_GEMM_SIMT = 0, 1
+DAG_TC_GIVEN, DAG_TC_WHOLE, DAG_TC_PER_KERNEL = 0, 1, 2
 
 
 class dag_buffer_desc(C.Structure):
@@ -47,6 +48,16 @@ class dag_options(C.Structure):
     _fields_ = [("timeout_ns", u64), ("trace", i32), ("max_ctas", i32), ("scheduler", i32),
                 ("tile_override", i32), ("node_cost_us", C.POINTER(f32)), ("debug_never_ready", i32),
                 ("use_graph", i32), ("autotune", i32), ("f32_gemm", i32), ("reserved", i32 * 4)]
+
+
+class dag_cq_options(C.Structure):
+    _fields_ = [("n_queues", i32), ("components", i32), ("fifo", i32), ("pad", i32), ("timeout_ns", u64),
+                ("node_start_us", C.POINTER(f32)), ("node_end_us", C.POINTER(f32))]
+
+
+class dag_cq_result(C.Structure):
+    _fields_ = [("device_us", C.c_double), ("host_us", C.c_double), ("gap_us", C.c_double),
+                ("n_components", i32), ("n_callbacks", i32)]
 
 
 class dag_copy_class(C.Structure):
@@ -106,6 +117,7 @@ _SIGS = {
     "dag_set_output": (i32, [C.c_void_p, C.c_int, C.c_void_p]),
     "dag_submit": (i32, [C.c_void_p, C.c_void_p]),
     "dag_submit_coarse": (i32, [C.c_void_p, C.c_void_p]),
+    "dag_submit_cq": (i32, [C.c_void_p, C.POINTER(dag_cq_options), C.POINTER(dag_cq_result)]),
     "dag_wait": (i32, [C.c_void_p, u64]),
     "dag_get_output": (i32, [C.c_void_p, C.c_int, C.c_void_p]),
     "dag_device_ptr": (C.c_void_p, [C.c_void_p, C.c_int, C.POINTER(C.c_int64)]),
@@ -251,6 +263,23 @@ def dag_submit(h, stream: int = 0) -> None:
 
 def dag_submit_coarse(h, stream: int = 0) -> None:
     check(lib().dag_submit_coarse(h, C.c_void_p(stream)), "dag_submit_coarse")
+
+
+def dag_submit_cq(h, n_queues: int = 1, components: int = 1, fifo: int = 0, timeout_ns: int = 0,
+                  n_nodes: int = 0):
+    """The paper's Alg. 1 on CUDA streams (synchronous).  Returns the result
+    struct and, if n_nodes > 0, per-kernel (start_us, end_us) arrays."""
+    import numpy as np
+    o = dag_cq_options(n_queues=n_queues, components=components, fifo=fifo, timeout_ns=timeout_ns)
+    ts = te = None
+    if n_nodes:
+        ts = np.zeros(n_nodes, np.float32)
+        te = np.zeros(n_nodes, np.float32)
+        o.node_start_us = ts.ctypes.data_as(C.POINTER(f32))
+        o.node_end_us = te.ctypes.data_as(C.POINTER(f32))
+    r = dag_cq_result()
+    check(lib().dag_submit_cq(h, C.byref(o), C.byref(r)), "dag_submit_cq")
+    return r, ts, te
 
 
 def dag_wait(h, timeout_ns: int = 30_000_000_000) -> int:

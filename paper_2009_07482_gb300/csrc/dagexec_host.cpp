@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -832,10 +833,19 @@ struct dag_handle {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   double tuned_us = 0.0;
+  // command-queue executor (dag_submit_cq): streams and per-kernel / per-buffer events
+  std::vector<cudaStream_t> cq_q;
+  std::vector<cudaEvent_t> cq_beg, cq_end, cq_buf;
+  cudaEvent_t cq_t0 = nullptr;
 };
 
 static void free_handle(dag_handle *h) {
   if (!h) return;
+  for (cudaStream_t q : h->cq_q) cudaStreamDestroy(q);
+  for (auto *v : {&h->cq_beg, &h->cq_end, &h->cq_buf})
+    for (cudaEvent_t e : *v)
+      if (e) cudaEventDestroy(e);
+  if (h->cq_t0) cudaEventDestroy(h->cq_t0);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->graph) cudaGraphDestroy(h->graph);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -1525,5 +1535,287 @@ dag_status dagx::plan_into_region(const dag_node_desc *nodes, int n_nodes, const
   xp.trace = nullptr;
   xp.trace_on = 0;
   xp.timeout_ns = P.opt.timeout_ns;
+  return DAG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// dag_submit_cq: the paper's Alg. 1 (schedule / setup_cq / cb) on CUDA streams
+// ---------------------------------------------------------------------------
+namespace {
+
+struct CqRun;
+struct CqArg {
+  CqRun *run;
+  int kernel;
+};
+
+// State shared between the schedule loop and the host callbacks (cb).
+struct CqRun {
+  std::mutex mu;
+  std::condition_variable cv;
+  std::vector<int> comp;              // kernel -> component
+  std::vector<int> end_left;          // component -> END kernels not yet finished
+  std::vector<int> pred_left;         // component -> predecessor components not yet finished
+  std::vector<std::vector<int>> csucc;
+  std::vector<int> ready;             // the task queue F
+  bool device_free = true;
+  int n_done = 0, n_callbacks = 0;
+  std::vector<CqArg> args;
+};
+
+void CUDART_CB cq_callback(void *p) {
+  CqArg *a = static_cast<CqArg *>(p);
+  CqRun *r = a->run;
+  std::lock_guard<std::mutex> lk(r->mu);
+  r->n_callbacks++;
+  const int c = r->comp[a->kernel];
+  if (--r->end_left[c] == 0) {  // T finished: release its successors and the device
+    r->n_done++;
+    for (int s : r->csucc[c])
+      if (--r->pred_left[s] == 0) r->ready.push_back(s);
+    r->device_free = true;
+  }
+  r->cv.notify_one();
+}
+
+}  // namespace
+
+extern "C" dag_status dag_submit_cq(dag_handle *h, const dag_cq_options *o, dag_cq_result *res) {
+  dag_status s = check_handle(h);
+  if (s) return s;
+  if (!o) return fail(DAG_EINVAL, "null options");
+  if (h->in_flight) return fail(DAG_EBUSY, "a submit is in flight");
+  if (o->n_queues < 1 || o->n_queues > 32) return fail(DAG_EINVAL, "n_queues %d not in 1..32", o->n_queues);
+  if (o->components < DAG_TC_GIVEN || o->components > DAG_TC_PER_KERNEL)
+    return fail(DAG_EINVAL, "bad components mode %d", o->components);
+  Plan &P = h->P;
+  Graph &g = P.g;
+  const int n = g.nn;
+
+  // ---- the task component partition and its graph ----
+  CqRun *run = new (std::nothrow) CqRun();
+  if (!run) return fail(DAG_ENOMEM, "host allocation");
+  std::vector<int> raw(n);
+  for (int v = 0; v < n; ++v)
+    raw[v] = o->components == DAG_TC_GIVEN ? g.nodes[v].component : o->components == DAG_TC_WHOLE ? 0 : v;
+  std::vector<int> ids(raw);
+  std::sort(ids.begin(), ids.end());
+  ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
+  const int nc = (int)ids.size();
+  run->comp.resize(n);
+  for (int v = 0; v < n; ++v) run->comp[v] = (int)(std::lower_bound(ids.begin(), ids.end(), raw[v]) - ids.begin());
+  const std::vector<int> &comp = run->comp;
+  std::vector<char> front(n, 1), end(n, 1);
+  run->csucc.assign(nc, {});
+  run->pred_left.assign(nc, 0);
+  run->end_left.assign(nc, 0);
+  for (int u = 0; u < n; ++u)
+    for (int v : g.succ[u]) {
+      if (comp[u] == comp[v]) { end[u] = 0; front[v] = 0; continue; }
+      std::vector<int> &cs = run->csucc[comp[u]];
+      if (std::find(cs.begin(), cs.end(), comp[v]) == cs.end()) { cs.push_back(comp[v]); run->pred_left[comp[v]]++; }
+    }
+  for (int v = 0; v < n; ++v) run->end_left[comp[v]] += end[v];
+  {  // the component graph must be acyclic (a convex partition), or the schedule cannot finish
+    std::vector<int> indeg(run->pred_left), stack;
+    for (int c = 0; c < nc; ++c)
+      if (!indeg[c]) stack.push_back(c);
+    int seen = 0;
+    while (!stack.empty()) {
+      const int c = stack.back();
+      stack.pop_back();
+      ++seen;
+      for (int d : run->csucc[c])
+        if (--indeg[d] == 0) stack.push_back(d);
+    }
+    if (seen != nc) { delete run; return fail(DAG_ECYCLE, "the task components form a cycle"); }
+  }
+  // priority of a component: the largest bottom-level rank among its FRONT kernels
+  std::vector<double> crank(nc, -1.0);
+  for (int v = 0; v < n; ++v)
+    if (front[v]) crank[comp[v]] = std::max(crank[comp[v]], P.rank.empty() ? 0.0 : P.rank[v]);
+  std::vector<std::vector<int>> members(nc);
+  for (int v : g.topo) members[comp[v]].push_back(v);
+
+  // ---- streams and events (created once per handle) ----
+  auto fail_cuda = [&](cudaError_t e) { delete run; return fail(DAG_EDEVICE, "CUDA: %s", cudaGetErrorString(e)); };
+  cudaError_t ce;
+  while ((int)h->cq_q.size() < o->n_queues) {
+    cudaStream_t q;
+    if ((ce = cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking))) return fail_cuda(ce);
+    h->cq_q.push_back(q);
+  }
+  if (!h->cq_t0) {  // the handle keeps them only once all exist (free_handle destroys the rest)
+    h->cq_beg.assign(n, nullptr);
+    h->cq_end.assign(n, nullptr);
+    h->cq_buf.assign(g.nb, nullptr);
+    for (int v = 0; v < n; ++v)
+      if ((ce = cudaEventCreate(&h->cq_beg[v])) || (ce = cudaEventCreate(&h->cq_end[v]))) return fail_cuda(ce);
+    for (int b = 0; b < g.nb; ++b)
+      if ((ce = cudaEventCreateWithFlags(&h->cq_buf[b], cudaEventDisableTiming))) return fail_cuda(ce);
+    if ((ce = cudaEventCreate(&h->cq_t0))) return fail_cuda(ce);
+  }
+  std::vector<char> need_up(g.nb, 0), uploaded(g.nb, 0);
+  std::vector<int> up_queue(g.nb, -1);
+  for (int b = 0; b < g.nb; ++b)
+    need_up[b] = h->resident_dirty[b] || (P.flag_of_root[b] >= 0 && h->host_in[b]);
+  ExecParams x = h->xp;
+  x.tiles = h->d_coarse;
+  run->args.resize(n);
+  for (int v = 0; v < n; ++v) run->args[v] = CqArg{run, v};
+
+  // ---- setup_cq + dispatch of one component ----
+  std::vector<std::vector<int>> writers(g.nb);
+  for (int v = 0; v < n; ++v) writers[g.root[g.nodes[v].out]].push_back(v);
+  std::vector<int> writers_left(g.nb, 0);
+  for (int b = 0; b < g.nb; ++b) writers_left[b] = (int)writers[b].size();
+  std::vector<int> qof(n, -1), order;  // order: components in dispatch order
+  std::vector<char> processed(n, 0);
+  int rr = 0;
+  auto setup_cq = [&](int c) -> cudaError_t {
+    std::vector<int> unprocessed;
+    for (int v : members[c])
+      if (front[v]) unprocessed.push_back(v);
+    while (!unprocessed.empty()) {
+      // the unprocessed kernel with the largest bottom-level rank (ties: topological order)
+      size_t pick = 0;
+      for (size_t i = 1; i < unprocessed.size(); ++i) {
+        const int a = unprocessed[i], b = unprocessed[pick];
+        const double ra = P.rank.empty() ? 0.0 : P.rank[a], rb = P.rank.empty() ? 0.0 : P.rank[b];
+        if (ra > rb || (ra == rb && g.topo_pos[a] < g.topo_pos[b])) pick = i;
+      }
+      const int k = unprocessed[pick];
+      unprocessed.erase(unprocessed.begin() + pick);
+      const int qi = rr++ % o->n_queues;
+      cudaStream_t q = h->cq_q[qi];
+      cudaError_t e;
+      // writes: isolated inputs of k (once per run), on k's queue
+      int in[3];
+      const int ni = g.inputs(k, in);
+      for (int i = 0; i < ni; ++i) {
+        const int b = g.root[in[i]];
+        if (need_up[b] && !uploaded[b]) {
+          if ((e = copy_h2d(h, b, q)) || (e = cudaEventRecord(h->cq_buf[b], q))) return e;
+          uploaded[b] = 1;
+          up_queue[b] = qi;
+        } else if (uploaded[b] && up_queue[b] != qi) {
+          if ((e = cudaStreamWaitEvent(q, h->cq_buf[b], 0))) return e;
+        }
+      }
+      // E_Q: predecessors inside T on other queues
+      for (int u : g.pred[k])
+        if (comp[u] == c && qof[u] != qi)
+          if ((e = cudaStreamWaitEvent(q, h->cq_end[u], 0))) return e;
+      // ndrange
+      if ((e = cudaEventRecord(h->cq_beg[k], q))) return e;
+      if (P.node_count[k] && (e = launch_coarse(x, P.node_first[k], P.node_count[k], q))) return e;
+      if ((e = cudaEventRecord(h->cq_end[k], q))) return e;
+      qof[k] = qi;
+      processed[k] = 1;
+      // read: a registered output, once its last writer is enqueued (writers of
+      // a root's column views on other queues of T are waited for; those of
+      // earlier components have finished)
+      const int ob = g.root[g.nodes[k].out];
+      if (h->host_out[ob] && --writers_left[ob] == 0) {
+        for (int u : writers[ob])
+          if (u != k && comp[u] == c && qof[u] != qi)
+            if ((e = cudaStreamWaitEvent(q, h->cq_end[u], 0))) return e;
+        const dag_buffer_desc &d = g.bufs[ob];
+        const size_t w = (size_t)d.cols * esize(d.dtype);
+        if ((e = cudaMemcpy2DAsync(h->host_out[ob], w, h->dptr[ob], (size_t)h->ld[ob] * esize(d.dtype), w, d.rows,
+                                   cudaMemcpyDeviceToHost, q)))
+          return e;
+      }
+      if (end[k] && (e = cudaLaunchHostFunc(q, cq_callback, &run->args[k]))) return e;
+      // successors in T whose predecessors in T are all processed
+      for (int w : g.succ[k]) {
+        if (comp[w] != c || processed[w] ||
+            std::find(unprocessed.begin(), unprocessed.end(), w) != unprocessed.end())
+          continue;
+        bool ok = true;
+        for (int u : g.pred[w]) ok &= comp[u] != c || processed[u];
+        if (ok) unprocessed.push_back(w);
+      }
+    }
+    return cudaSuccess;
+  };
+
+  // ---- schedule ----
+  if ((ce = cudaEventRecord(h->cq_t0, h->cq_q[0]))) return fail_cuda(ce);
+  for (int i = 1; i < o->n_queues; ++i)
+    if ((ce = cudaStreamWaitEvent(h->cq_q[i], h->cq_t0, 0))) return fail_cuda(ce);
+  const auto t_host0 = std::chrono::steady_clock::now();
+  const uint64_t limit = o->timeout_ns ? o->timeout_ns : 10000000000ull;
+  {
+    std::unique_lock<std::mutex> lk(run->mu);
+    for (int c = 0; c < nc; ++c)
+      if (!run->pred_left[c]) run->ready.push_back(c);
+    while (run->n_done < nc) {
+      while (run->device_free && !run->ready.empty()) {
+        size_t pick = 0;
+        for (size_t i = 1; i < run->ready.size(); ++i) {
+          const int a = run->ready[i], b = run->ready[pick];
+          if (o->fifo ? a < b : (crank[a] > crank[b] || (crank[a] == crank[b] && a < b))) pick = i;
+        }
+        const int c = run->ready[pick];
+        run->ready.erase(run->ready.begin() + pick);
+        run->device_free = false;
+        order.push_back(c);
+        lk.unlock();
+        const cudaError_t e = setup_cq(c);
+        lk.lock();
+        if (e) {
+          lk.unlock();
+          for (cudaStream_t q : h->cq_q) cudaStreamSynchronize(q);  // callbacks already enqueued finish
+          h->poisoned = DAG_EDEVICE;
+          return fail(DAG_EDEVICE, "setup_cq: %s", cudaGetErrorString(e));  // run leaked: callbacks may hold it
+        }
+      }
+      if (run->n_done == nc) break;
+      if (!run->cv.wait_for(lk, std::chrono::nanoseconds(limit),
+                            [&] { return run->n_done == nc || (run->device_free && !run->ready.empty()); })) {
+        h->poisoned = DAG_ETIMEOUT;
+        return fail(DAG_ETIMEOUT, "no callback within the limit");  // run leaked: callbacks may still come
+      }
+    }
+  }
+  const double host_us =
+      std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t_host0).count();
+  for (cudaStream_t q : h->cq_q)
+    if ((ce = cudaStreamSynchronize(q))) {
+      h->poisoned = DAG_EDEVICE;
+      delete run;
+      return fail(DAG_EDEVICE, "device error: %s", cudaGetErrorString(ce));
+    }
+  for (int b = 0; b < g.nb; ++b)
+    if (uploaded[b] && (g.bufs[b].flags & DAG_BUF_RESIDENT)) h->resident_dirty[b] = 0;
+
+  // ---- timings ----
+  std::vector<float> t_beg(n, 0.f), t_end(n, 0.f);
+  double dev = 0.0;
+  for (int v = 0; v < n; ++v) {
+    cudaEventElapsedTime(&t_beg[v], h->cq_t0, h->cq_beg[v]);
+    cudaEventElapsedTime(&t_end[v], h->cq_t0, h->cq_end[v]);
+    t_beg[v] *= 1000.f;
+    t_end[v] *= 1000.f;
+    dev = std::max(dev, (double)t_end[v]);
+    if (o->node_start_us) o->node_start_us[v] = t_beg[v];
+    if (o->node_end_us) o->node_end_us[v] = t_end[v];
+  }
+  double gap = 0.0;
+  for (size_t i = 1; i < order.size(); ++i) {
+    double last_end = 0.0, first_beg = 1e30;
+    for (int v : members[order[i - 1]]) last_end = std::max(last_end, (double)t_end[v]);
+    for (int v : members[order[i]]) first_beg = std::min(first_beg, (double)t_beg[v]);
+    gap += std::max(0.0, first_beg - last_end);
+  }
+  if (res) {
+    res->device_us = dev;
+    res->host_us = host_us;
+    res->gap_us = gap;
+    res->n_components = nc;
+    res->n_callbacks = run->n_callbacks;
+  }
+  delete run;
   return DAG_OK;
 }

@@ -122,6 +122,13 @@ class Dag:
         (self.submit_coarse if coarse else self.submit)()
         abi.check(self.wait(), "dag_wait")
 
+    def run_cq(self, n_queues: int = 1, components: int = abi.DAG_TC_WHOLE, fifo: int = 0, times: bool = False):
+        """The paper's Alg. 1 on CUDA streams (dag_submit_cq), synchronous.
+        Returns the dag_cq_result, plus per-kernel (start_us, end_us) arrays
+        when times is set."""
+        r, ts, te = abi.dag_submit_cq(self.h, n_queues, components, fifo, 0, len(self.w.nodes) if times else 0)
+        return (r, ts, te) if times else r
+
     def trace(self):
         return abi.dag_trace_get(self.h)
 

@@ -60,6 +60,7 @@ class Node:
     scale: float = 1.0
     batch: int = 1
     name: str = ""
+    component: int = 0  # task component id (the paper's partition T of the kernels)
 
 
 @dataclass
@@ -269,6 +270,45 @@ def encoder_block(batch: int = 8, seq: int = 256, d_model: int = 1024, heads: in
     b2 = w.buf(1, d_model, F32, "input", ("normal", nxt(), 0.02), "b2")
     Y = w.buf(T, d_model, F32, "output", name="Y")
     w.node("gemm", H, Y, b=W2, bias=b2, name="ffn2")
+    return w
+
+
+def transformer_heads(heads: int = 16, beta: int = 256, dtype: str = F32, seed: int = 4,
+                      softmax_scale: float = 1.0) -> Workload:
+    """The paper's transformer-layer DAG of §6 (its Experiments 1-3): every
+    matrix beta x beta; per head h: Q=X.Wq, K=X.Wk, V=X.Wv, A=Q.K^T (K read
+    as a K-major operand: the transpose kernel is fused away), B=softmax(A),
+    C=B.V, Z[:, h] = C.Wh (heads concatenated in place).  Each head is one
+    task component (the paper's clustering partition).  X ~ U[-1,1), weights
+    N(0, 0.02); the softmax scale defaults to the paper's literal form (1).
+    """
+    w = Workload(f"transformer_heads_h{heads}_b{beta}_{dtype}")
+    s = 0
+
+    def nxt():
+        nonlocal s
+        s += 1
+        return _seed(seed, s)
+
+    X = w.buf(beta, beta, dtype, "input", ("uniform", nxt()), "X")
+    Z = w.buf(beta, heads * beta, dtype, "output", name="Z")
+    for h in range(heads):
+        proj = []
+        for nm in ("q", "k", "v"):
+            Wt = w.buf(beta, beta, dtype, "input", ("normal", nxt(), 0.02), f"W{nm}{h}")
+            o = w.buf(beta, beta, dtype, "inter", name=f"{nm}{h}")
+            w.node("gemm", X, o, b=Wt, name=f"proj_{nm}{h}", component=h)
+            proj.append(o)
+        Q, Kb, V = proj
+        A = w.buf(beta, beta, F32, "inter", name=f"A{h}")
+        w.node("gemm", Q, A, b=Kb, trans_b=1, name=f"qk{h}", component=h)
+        B = w.buf(beta, beta, dtype, "inter", name=f"B{h}")
+        w.node("softmax", A, B, scale=softmax_scale, name=f"softmax{h}", component=h)
+        C = w.buf(beta, beta, dtype, "inter", name=f"C{h}")
+        w.node("gemm", B, C, b=V, name=f"bv{h}", component=h)
+        Wh = w.buf(beta, beta, dtype, "input", ("normal", nxt(), 0.02), f"Wh{h}")
+        Zh = w.buf(beta, beta, dtype, "inter", view_of=Z, col_offset=h * beta, name=f"Z{h}")
+        w.node("gemm", C, Zh, b=Wh, name=f"cw{h}", component=h)
     return w
 
 
