@@ -132,13 +132,45 @@ def run_exp1(args):
             row["speedup_persistent_over_best"] = row["best_us"] / row["persistent_us"]
             rows.append(row)
             d.close()
+        # Experiments 2-3: H = 16, beta 64..512; clustering (best q) against the
+        # dynamic coarse policies with a host callback per kernel: eager (F by
+        # rank) and FIFO order.  HEFT on a single device places every kernel on
+        # it, so it reduces to the rank-ordered list (eager) here.
+        rows23 = []
+        for beta in (64, 128, 256, 512):
+            w = transformer_heads(16, beta)
+            d = Dag(w, options(), resident_inputs=True)
+            d.set_inputs(w.make_inputs(_INPUTS))
+            pers = []
+            for i in range(23):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                d.submit(stream.cuda_stream)
+                b.record(stream)
+                abi.check(d.wait(), "wait")
+                if i >= 3:
+                    pers.append(a.elapsed_time(b) * 1e3)
+            row = {"beta": beta, "persistent_us": statistics.median(pers)}
+            clus = {q: statistics.median(d.run_cq(n_queues=q, components=abi.DAG_TC_GIVEN).device_us
+                                         for _ in range(4)) for q in (1, 2, 3, 4, 5)}
+            row["clustering_best_q"] = min(clus, key=clus.get)
+            row["clustering_us"] = clus[row["clustering_best_q"]]
+            for name, fifo in (("eager_rank_us", 0), ("eager_fifo_us", 1)):
+                rs = [d.run_cq(n_queues=1, components=abi.DAG_TC_PER_KERNEL, fifo=fifo) for _ in range(4)]
+                row[name] = statistics.median(r.device_us for r in rs)
+                if not fifo:
+                    row["eager_gap_us"] = statistics.median(r.gap_us for r in rs)
+            row["speedup_clustering_over_eager"] = row["eager_rank_us"] / row["clustering_us"]
+            row["speedup_persistent_over_clustering"] = row["clustering_us"] / row["persistent_us"]
+            rows23.append(row)
+            d.close()
     last = rows[-1]
     line = {"metric": "DAG makespan (us), paper §6 Experiment 1 transformer DAGs (beta 256, f32)",
             "value": last["persistent_us"], "unit": "us", "higher_is_better": False, "n_gpus": 1,
             "dtype": "f32", "data": "synthetic (seeded SplitMix64)",
             "config": {"workload": "transformer_heads H in {1,2,4,8,16}, beta 256; value = persistent executor at H=16",
                        "f32_gemm": "tensor cores (3 x TF32 split)"},
-            "sweep": rows, "clocks": clk.summary()}
+            "sweep": rows, "exp2_3": rows23, "clocks": clk.summary()}
     print(json.dumps(line))
     return 0
 

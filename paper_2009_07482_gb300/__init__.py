@@ -3,9 +3,10 @@
 The library proper is ``libdagexec.so`` (C ABI in ``include/dagexec.h``): a
 host planner plus one persistent CUDA executor kernel.  This package holds its
 sources (``csrc/``), the build step (``build.py``), the ctypes binding
-(``_binding.py``, same names as the C ABI) and ``dag.py``, a small convenience
+(``_binding.py``, same names as the C ABI), ``dag.py``, a small convenience
 layer that turns a workload description into the ABI's structs and moves
-numpy arrays in and out.
+numpy arrays in and out, and ``spec.py``, the JSON specification frontend
+(paper §4.A) with example files in ``specs/``.
 """
 from . import _binding as abi  # noqa: F401
 from .dag import Dag, describe  # noqa: F401

@@ -38,7 +38,8 @@ def describe(w, resident_inputs: bool = False, streamed=None):
     for n in w.nodes:
         nodes.append(abi.dag_node_desc(_OP[n.op], n.a, n.b, n.bias, n.out, n.trans_b, _ACT[n.act],
                                        float(n.scale), n.batch, getattr(n, "component", 0)))
-    return nodes, [], bufs
+    edges = [abi.dag_edge(*e) for e in getattr(w, "edges", [])]  # optional explicit k_i,b_r -> k_j,b_s
+    return nodes, edges, bufs
 
 
 def options(**kw) -> abi.dag_options:

@@ -133,3 +133,25 @@ def test_cq_rejects_a_cyclic_partition():
         d.run_cq(n_queues=1, components=abi.DAG_TC_GIVEN)
     d.run()  # the handle stays usable
     d.close()
+
+
+@pytest.mark.parametrize("name,sym", [("fork_join.json", {"N": 192}), ("transformer_head.json", {"beta": 128})])
+def test_spec_files_run_on_both_executors(name, sym):
+    """A JSON specification (paper §4.A) runs as written: its explicit edges
+    pass dag_create's check, its cq and tc drive Alg. 1 on streams, and both
+    executors match the oracle with the same bits."""
+    import os
+    from paper_2009_07482_gb300 import spec
+    from tests.conftest import ROOT
+    sd = spec.load(os.path.join(ROOT, "paper_2009_07482_gb300", "specs", name), sym)
+    w = sd.to_workload()
+    ins = w.make_inputs()
+    d = Dag(w, options(trace=1), resident_inputs=True)
+    d.set_inputs(ins)
+    d.run()
+    base = _outputs(d, w)
+    compare(w, base, oracle.run(w, ins))
+    r = d.run_cq(n_queues=sd.queues, components=abi.DAG_TC_GIVEN)
+    assert r.n_components == len(set(n.component for n in sd.nodes))
+    assert bits_equal(base, _outputs(d, w))
+    d.close()
