@@ -37,7 +37,6 @@ static_assert(kSmemBytes <= 232448, "shared memory budget");
 struct WorkerShared {
   int32_t tile;
   int32_t ok;
-  int32_t stage_ok;  // f32 tensor-core tiles: the next stage arrived
 };
 
 __device__ __forceinline__ void record_error(const ExecParams &p, uint32_t code, int tile) {
@@ -208,7 +207,7 @@ __device__ __forceinline__ void run_workers(const ExecParams &p, uint8_t *smem, 
         stage_bias(td, np, ctl);
         const uint32_t acc = ctl->tmem_base + accb * kAccCols;
         if (td.op == T_GEMM_TF32) {
-          const bool mine = tf32_worker_loop(np, smem, ctl, fs, acc, &ws->stage_ok, globaltimer() + p.timeout_ns);
+          const bool mine = tf32_worker_loop(np, smem, ctl, fs, acc, globaltimer() + p.timeout_ns);
           if (!mine) ws->ok = 0;  // any warp that timed out fails the tile
           worker_sync();
           if (p.trace_on && wt == 0) p.trace[t].stamp[S_ACC] = globaltimer();
@@ -284,7 +283,7 @@ __global__ void __launch_bounds__(kThreads, 1) dag_exec_kernel(const __grid_cons
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&ctl->full[s], 1);
       mbar_init(&ctl->empty[s], 1);
-      mbar_init(&ctl->split[s], 1);
+      mbar_init(&ctl->split[s], kWorkers / 32);  // one arrival per worker warp
       ctl->issued[s] = 0;
     }
     for (int b = 0; b < 2; ++b) {

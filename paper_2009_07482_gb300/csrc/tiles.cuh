@@ -162,16 +162,19 @@ __device__ __forceinline__ bool gemm_mma(const TileDesc &t, const NodeParams &np
 
 // ---------------------------------------------------------------------------
 // f32 GEMM tile, 128 x 64, on the tensor cores with the 3 x TF32 split: each
-// operand x = hi + lo with hi = tf32(x), lo = tf32(x - hi), and
-// A.B ~= Ahi.Bhi + Ahi.Blo + Alo.Bhi (the dropped Alo.Blo and the rounding of
-// lo are ~2^-22 relative), accumulated in f32 in TMEM.  One stage holds one
-// K block of 32 (128-byte rows):
-//   A area (16 KiB): A, K-major; split in place into Ahi
-//   B area: [0, 8K) B (K-major after the split; Bhi), [8K, 16K) Blo,
-//           [16K, 32K) Alo
-// The producer loads raw f32 with TMA; the workers round in place, transpose
-// an MN-major B into K-major, and signal split[s]; the MMA issuer then runs
-// three tf32 MMAs per K step of 8.
+// operand x = hi + lo, and A.B ~= Ahi.Bhi + Ahi.Blo + Alo.Bhi accumulated in
+// f32 in TMEM.  The tensor cores read a 32-bit operand as tf32 by dropping
+// its low 13 bits, so hi is x itself as stored (read as trunc(x)) and
+// lo = x - trunc(x), exact in f32 and read with its top 11 significant bits:
+// the dropped Alo.Blo and the truncation of lo are ~2^-21 relative per
+// product.  One stage holds one K block of 32 (128-byte rows):
+//   A area (16 KiB): A, K-major, as loaded (Ahi)
+//   B area: [0, 8K) B, K-major (an MN-major B is transposed in place; Bhi),
+//           [8K, 16K) Blo, [16K, 32K) Alo
+// The producer loads raw f32 with TMA; each worker warp splits its share of
+// the stage (an MN-major box is transposed by one warp) and arrives on
+// split[s] (8 arrivals); the MMA issuer then runs three tf32 MMAs per K step
+// of 8.
 // ---------------------------------------------------------------------------
 constexpr int kTf32BBytes = kTf32BN * kBKF * 4;  // 8 KiB
 constexpr int kTf32Blo = kTf32BBytes;            // offsets in the B area
@@ -206,86 +209,68 @@ __device__ __forceinline__ bool tf32_produce(const ExecParams &p, const TileDesc
   return true;
 }
 
-// tf32 rounding of an f32 bit pattern: round to nearest, ties away from zero,
-// on the 13 dropped mantissa bits (the value's low 13 bits become zero, so
-// the tensor cores read it exactly)
-__device__ __forceinline__ uint32_t tf32_bits(uint32_t u) { return (u + 0x1000u) & 0xFFFFE000u; }
-
-// hi/lo split of 4 consecutive f32 (one 16-byte chunk)
-__device__ __forceinline__ void split1(uint32_t x, uint32_t &hi, uint32_t &lo) {
-  hi = tf32_bits(x);
-  lo = tf32_bits(__float_as_uint(__uint_as_float(x) - __uint_as_float(hi)));
+// lo of an f32 bit pattern: x minus its truncation to tf32 (exact)
+__device__ __forceinline__ uint32_t tf32_lo(uint32_t u) {
+  return __float_as_uint(__uint_as_float(u) - __uint_as_float(u & 0xFFFFE000u));
 }
-__device__ __forceinline__ void split4(uint4 x, uint4 &hi, uint4 &lo) {
-  split1(x.x, hi.x, lo.x);
-  split1(x.y, hi.y, lo.y);
-  split1(x.z, hi.z, lo.z);
-  split1(x.w, hi.w, lo.w);
+__device__ __forceinline__ uint4 tf32_lo4(uint4 x) {
+  return make_uint4(tf32_lo(x.x), tf32_lo(x.y), tf32_lo(x.z), tf32_lo(x.w));
 }
 
-// Split one filled stage (the 256 workers, wt = 0..255).  A and a K-major B:
-// element-wise, hi in place and lo at the same layout offset.  An MN-major B
-// is transposed in place: box j holds columns 32j..32j+31 as 32 K rows of 128
-// bytes, chunk c of row k at (c ^ (k % 8)); threads 0..127 each read one
-// 4 (K) x 4 (N) block, all workers sync, then each writes its block K-major
-// (row n, chunk k/4 at ((k/4) ^ (n % 8))).
-__device__ __forceinline__ void tf32_split_stage(uint8_t *a, uint8_t *b, int trans_b, int wt) {
-  constexpr int kA = kStageA / 16 / kWorkers;       // 4 chunks of A per thread
-  constexpr int kB = kTf32BBytes / 16 / kWorkers;   // 2 chunks of B per thread
-  uint4 *A4 = reinterpret_cast<uint4 *>(a);
-  uint4 *Alo = reinterpret_cast<uint4 *>(b + kTf32Alo);
+// One worker warp's share of splitting a filled stage (wid = worker warp
+// 0..7).  A and a K-major B: lo of each 16-byte chunk at the same layout
+// offset.  An MN-major B: box j (columns 32j..32j+31 as 32 K rows of 128
+// bytes, chunk c of row k at (c ^ (k % 8))) is transposed in place by worker
+// warp j alone -- the 4 (K) x 4 (N) blocks of one box only overwrite one
+// another -- into K-major rows 32j..32j+31 (row n, chunk k/4 at
+// ((k/4) ^ (n % 8))), with its lo alongside.
+__device__ __forceinline__ void tf32_split_warp(uint8_t *a, uint8_t *b, int trans_b, int wid, int lane) {
+  constexpr int kAw = kStageA / 16 / 8;        // 128 chunks of A per warp
+  uint4 *A4 = reinterpret_cast<uint4 *>(a) + wid * kAw;
+  uint4 *Alo = reinterpret_cast<uint4 *>(b + kTf32Alo) + wid * kAw;
+  uint4 xa[kAw / 32];
+#pragma unroll
+  for (int j = 0; j < kAw / 32; ++j) xa[j] = A4[lane + 32 * j];
+#pragma unroll
+  for (int j = 0; j < kAw / 32; ++j) Alo[lane + 32 * j] = tf32_lo4(xa[j]);
   uint4 *B4 = reinterpret_cast<uint4 *>(b);
   uint4 *Blo = reinterpret_cast<uint4 *>(b + kTf32Blo);
-  uint4 xa[kA], xb[kB];
-#pragma unroll
-  for (int j = 0; j < kA; ++j) xa[j] = A4[wt + j * kWorkers];
   if (trans_b) {
+    constexpr int kBw = kTf32BBytes / 16 / 8;  // 64 chunks of B per warp
 #pragma unroll
-    for (int j = 0; j < kB; ++j) xb[j] = B4[wt + j * kWorkers];
-  }
-#pragma unroll
-  for (int j = 0; j < kA; ++j) {
-    uint4 hi, lo;
-    split4(xa[j], hi, lo);
-    A4[wt + j * kWorkers] = hi;
-    Alo[wt + j * kWorkers] = lo;
-  }
-  if (trans_b) {
-#pragma unroll
-    for (int j = 0; j < kB; ++j) {
-      uint4 hi, lo;
-      split4(xb[j], hi, lo);
-      B4[wt + j * kWorkers] = hi;
-      Blo[wt + j * kWorkers] = lo;
+    for (int j = 0; j < kBw / 32; ++j) {
+      const int i = wid * kBw + lane + 32 * j;
+      Blo[i] = tf32_lo4(B4[i]);
     }
     return;
   }
-  const bool mine = wt < 128;  // 8 K quads x 16 N quads
-  const int kq = wt & 7, nq = (wt >> 3) & 15;
-  uint4 v[4];
-  if (mine) {
-    const int j = nq >> 3, c = nq & 7;
+  if (wid >= kTf32BN / 32) return;
+  // box `wid`: 64 blocks (8 K quads x 8 N quads), two per lane
+  uint4 v[2][4];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int t = lane + 32 * u, kq = t & 7, c = t >> 3;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const int k = 4 * kq + r;
-      v[r] = B4[(j * 4096 + k * 128 + ((c ^ (k & 7)) << 4)) >> 4];
+      v[u][r] = B4[(wid * 4096 + k * 128 + ((c ^ (k & 7)) << 4)) >> 4];
     }
   }
-  worker_sync();  // every block read before any is overwritten
-  if (mine) {
+  __syncwarp();  // the whole box is read before any of it is overwritten
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int t = lane + 32 * u, kq = t & 7, c = t >> 3;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int n = 4 * nq + q;
+      const int n = 32 * wid + 4 * c + q;
       uint4 col;
-      col.x = q == 0 ? v[0].x : q == 1 ? v[0].y : q == 2 ? v[0].z : v[0].w;
-      col.y = q == 0 ? v[1].x : q == 1 ? v[1].y : q == 2 ? v[1].z : v[1].w;
-      col.z = q == 0 ? v[2].x : q == 1 ? v[2].y : q == 2 ? v[2].z : v[2].w;
-      col.w = q == 0 ? v[3].x : q == 1 ? v[3].y : q == 2 ? v[3].z : v[3].w;
-      uint4 hi, lo;
-      split4(col, hi, lo);
+      col.x = q == 0 ? v[u][0].x : q == 1 ? v[u][0].y : q == 2 ? v[u][0].z : v[u][0].w;
+      col.y = q == 0 ? v[u][1].x : q == 1 ? v[u][1].y : q == 2 ? v[u][1].z : v[u][1].w;
+      col.z = q == 0 ? v[u][2].x : q == 1 ? v[u][2].y : q == 2 ? v[u][2].z : v[u][2].w;
+      col.w = q == 0 ? v[u][3].x : q == 1 ? v[u][3].y : q == 2 ? v[u][3].z : v[u][3].w;
       const int o = (n * 128 + ((kq ^ (n & 7)) << 4)) >> 4;
-      B4[o] = hi;
-      Blo[o] = lo;
+      B4[o] = col;
+      Blo[o] = tf32_lo4(col);
     }
   }
 }
@@ -332,12 +317,12 @@ __device__ __forceinline__ bool tf32_mma(const NodeParams &np, uint8_t *smem, Sm
   return true;
 }
 
-// Worker side of an f32 tile: for each K block, split its stage (then the
-// MMA issuer may run it) and add up the partial of the K block kLag earlier
-// (each warp: its TMEM lane quadrant, columns half*32 .. +32 of the 64); at
-// the end the sum goes to columns 0..63 of the accumulator for the epilogue.
-// Waits are taken by the leader (wt == 0) or a warp's lane 0 and shared, so
-// all workers reach the same barriers; false if any wait ran out.
+// Worker side of an f32 tile: each worker warp, on its own, for each K
+// block splits its share of the stage (then arrives on split[s]; the MMA
+// issuer needs all 8) and adds up the partial of the K block kLag earlier
+// (its TMEM lane quadrant, columns half*32 .. +32 of the 64); at the end the
+// sum goes to columns 0..63 of the accumulator for the epilogue.  Waits are
+// taken by lane 0 and shared within the warp.  false if a wait ran out.
 constexpr int kLag = 2;
 static_assert(kLag < kParts, "the MMA issuer runs up to kParts partials ahead");
 
@@ -348,11 +333,10 @@ struct Tf32State {
 };
 
 __device__ __forceinline__ bool tf32_worker_loop(const NodeParams &np, uint8_t *smem, SmemCtl *ctl, Tf32State &fs,
-                                                 uint32_t tmem_acc, volatile int32_t *shared_ok, uint64_t deadline) {
-  const int wt = threadIdx.x - kWorkerBase;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int half = (wt >> 5) >> 2;
-  const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+                                                 uint32_t tmem_acc, uint64_t deadline) {
+  const int wid = (threadIdx.x - kWorkerBase) >> 5, lane = threadIdx.x & 31;
+  const int half = wid >> 2;
+  const uint32_t lanes = (uint32_t)((threadIdx.x >> 5 & 3) * 32) << 16;
   const int kiters = (np.K + kBKF - 1) / kBKF;
   const int trans_b = np.trans_b;
   uint8_t *sA = smem;
@@ -360,31 +344,31 @@ __device__ __forceinline__ bool tf32_worker_loop(const NodeParams &np, uint8_t *
   float sum[32];
 #pragma unroll
   for (int i = 0; i < 32; ++i) sum[i] = 0.0f;
-  bool ok = true, drain_ok = true;
+  bool ok = true;
   for (int kb = 0; kb < kiters + kLag; ++kb) {
     if (kb < kiters) {
-      if (wt == 0) *shared_ok = ok && stage_wait_use(ctl, fs.st.idx, fs.pass, deadline) ? 1 : 0;
-      worker_sync();
-      ok = *shared_ok != 0;
       if (ok) {
-        tf32_split_stage(sA + fs.st.idx * kStageA, sB + fs.st.idx * kStageB, trans_b, wt);
-        fence_proxy_async_shared();  // generic writes -> visible to the tensor cores
-      } else if (!trans_b) {
-        worker_sync();  // the split's own barrier
+        int w = 0;
+        if (lane == 0) w = stage_wait_use(ctl, fs.st.idx, fs.pass, deadline) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, w, 0) != 0;
       }
-      worker_sync();
-      if (wt == 0 && ok) mbar_arrive(&ctl->split[fs.st.idx]);
+      if (ok) {
+        tf32_split_warp(sA + fs.st.idx * kStageA, sB + fs.st.idx * kStageB, trans_b, wid, lane);
+        fence_proxy_async_shared();  // generic writes -> visible to the tensor cores
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ctl->split[fs.st.idx]);
+      }
       fs.st.next(kStages);
       if (fs.st.idx == 0) ++fs.pass;
     }
     if (kb >= kLag) {
       const uint32_t ps = fs.pq % kParts;
-      if (drain_ok) {
+      if (ok) {
         int w = 0;
         if (lane == 0) w = mbar_wait(&ctl->pfull[ps], (fs.pq / kParts) & 1u, deadline) ? 1 : 0;
-        drain_ok = __shfl_sync(0xffffffffu, w, 0) != 0;
+        ok = __shfl_sync(0xffffffffu, w, 0) != 0;
       }
-      if (drain_ok) {
+      if (ok) {
         tc_fence_after();
         float v[32];
         tmem_ld32(tmem_acc + lanes + ps * kTf32BN + half * 32, v);
@@ -397,11 +381,11 @@ __device__ __forceinline__ bool tf32_worker_loop(const NodeParams &np, uint8_t *
       ++fs.pq;
     }
   }
-  if (ok && drain_ok) {
+  if (ok) {
     tmem_st32(tmem_acc + lanes + half * 32, sum);
     tc_fence_before();
   }
-  return ok && drain_ok;
+  return ok;
 }
 
 // Epilogue (workers): TMEM accumulator -> scale, bias, activation, cast ->
