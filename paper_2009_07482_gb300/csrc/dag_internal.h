@@ -25,8 +25,9 @@ enum TileOp : int32_t {
 enum F32Cfg : int32_t { F32_64x64 = 0, F32_128x64 = 1, F32_128x128 = 2 };
 
 // CTA layout: warp 0 = scheduler + TMA producer, warp 1 = MMA issuer,
-// warps 2-3 idle, warps 4-11 = 256 worker threads (GEMM epilogues, the
-// operand split of f32 tensor-core tiles, and every SIMT tile).
+// warp 2 = releaser (publishes finished tiles to the dependency counters),
+// warp 3 idle, warps 4-11 = 256 worker threads (GEMM epilogues, the operand
+// split of f32 tensor-core tiles, and every SIMT tile).
 constexpr int kThreads = 384;
 constexpr int kWorkerBase = 128;    // first worker thread
 constexpr int kWorkers = 256;       // worker threads
@@ -42,6 +43,7 @@ constexpr int kStageB = kMaxBN * kBK * 2;     // 32 KiB
 constexpr int kAccCols = 256;                 // one 128 x 256 f32 accumulator
 constexpr int kTmemCols = 2 * kAccCols;       // double-buffered accumulators
 constexpr int kSlots = 2;                     // scheduler -> MMA / workers tile ring
+constexpr int kRelSlots = 4;                  // workers -> releaser ring of finished tiles
 constexpr int kWorkerScratch = 32 * 1024;     // per-CTA worker scratch: epilogue staging / f32 tiles
 constexpr int kEpiRows = 32;                  // epilogue store box: 32 rows x 128 bytes per warp
 

@@ -525,7 +525,7 @@ static void make_tiles(Plan &P) {
     } else {
       // at most 32K and at least 4K elements per tile, split further while
       // the level has fewer than its share of two tiles per SM
-      const double share = 2.0 * P.n_sm * ((double)R * C) / std::max(1.0, level_elems[dep[v]]);
+      const double share = 1.0 * P.n_sm * ((double)R * C) / std::max(1.0, level_elems[dep[v]]);
       int rows = 256;
       while (rows > 1 && (long)rows * C > 32768) rows /= 2;
       while (rows > 1 && (double)((R + rows - 1) / rows) < share && (long)(rows / 2) * C >= 4096) rows /= 2;

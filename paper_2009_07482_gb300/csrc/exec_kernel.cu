@@ -174,6 +174,41 @@ __device__ __forceinline__ void run_mma(const ExecParams &p, uint8_t *smem, Smem
 }
 
 // ---------------------------------------------------------------------------
+// releaser (warp 2, lane 0): publishes each finished tile -- one gpu-scope
+// release fence, then a relaxed increment of every counter the tile
+// releases -- while the workers already run the next tile.  The workers'
+// writes are ordered before the hand-over by their barrier and the ring's
+// mbarrier (release / acquire at CTA scope), and the fence is cumulative.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void run_releaser(const ExecParams &p, SmemCtl *ctl) {
+  Ring r = {0u, 0u};
+  const uint64_t slot_limit = 2 * p.timeout_ns + 1000000000ull;
+  for (;;) {
+    if (!mbar_wait(&ctl->rel_full[r.idx], r.phase, globaltimer() + slot_limit)) {
+      ctl->fail = 1;
+      return;
+    }
+    const RelSlot s = ctl->rel[r.idx];
+    mbar_arrive(&ctl->rel_empty[r.idx]);
+    r.next(kRelSlots);
+    if (s.t < 0) return;
+    const TileDesc &td = p.tiles[s.t];
+    if (p.trace_on) {
+      TraceRec &tr = p.trace[s.t];
+      tr.start_ticket = s.start_ticket;
+      tr.end_ticket = atomicAdd(&p.ctrl->ticket, 1u);  // drawn before the release (the fence orders it)
+      tr.smid = smid();
+      tr.tile = (uint32_t)s.t;
+      tr.stamp[S_WORK] = s.t_work;
+    }
+    fence_acq_rel_gpu();
+    if (p.mode == 0)
+      for (int i = 0; i < td.rel_count; ++i) red_relaxed_add(&p.counters[p.rels[td.rel_begin + i]], 1u);
+    if (p.trace_on) p.trace[s.t].stamp[S_END] = globaltimer();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // workers (256 threads); every decision is taken by the leader and broadcast
 // through shared memory, so all workers reach the same named barriers
 // ---------------------------------------------------------------------------
@@ -184,6 +219,15 @@ __device__ __forceinline__ void run_workers(const ExecParams &p, uint8_t *smem, 
   Tf32State fs = {{0u, 0u}, 0u, 0u};  // the workers split f32 stages and add up their partials
   float *fsm = reinterpret_cast<float *>(smem + kSmemStages);
   const uint64_t slot_limit = 2 * p.timeout_ns + 1000000000ull;
+  Ring rel = {0u, 0u};
+  // hand a finished tile (or -1: no more) to the releaser (worker leader only)
+  auto hand_over = [&](int t, uint32_t start_ticket, uint64_t t_work) -> bool {
+    if (!mbar_wait(&ctl->rel_empty[rel.idx], rel.phase ^ 1u, globaltimer() + slot_limit)) return false;
+    ctl->rel[rel.idx] = RelSlot{t, start_ticket, t_work};
+    mbar_arrive(&ctl->rel_full[rel.idx]);
+    rel.next(kRelSlots);
+    return true;
+  };
   for (;;) {
     if (wt == 0) {
       const bool ok = mbar_wait(&ctl->slot_full[slot.idx], slot.phase, globaltimer() + slot_limit);
@@ -193,7 +237,10 @@ __device__ __forceinline__ void run_workers(const ExecParams &p, uint8_t *smem, 
     worker_sync();
     const int t = ws->tile;
     if (t < 0) {
-      if (t == -2 && wt == 0) ctl->fail = 1;
+      if (wt == 0) {
+        if (t == -2) ctl->fail = 1;
+        hand_over(-1, 0u, 0ull);
+      }
       return;
     }
     const TileSlot sl = ctl->slot[slot.idx];
@@ -251,19 +298,9 @@ __device__ __forceinline__ void run_workers(const ExecParams &p, uint8_t *smem, 
       if (!ok) {
         record_error(p, tc ? E_PIPE_TIMEOUT : E_BAD_TILE, t);
         ctl->fail = 1;
-      } else {
-        __threadfence();
-        if (p.trace_on) {
-          TraceRec &r = p.trace[t];
-          r.start_ticket = sl.start_ticket;
-          r.end_ticket = atomicAdd(&p.ctrl->ticket, 1u);  // drawn before the release
-          r.smid = smid();
-          r.tile = (uint32_t)t;
-          r.stamp[S_WORK] = t_work;
-        }
-        if (p.mode == 0)
-          for (int i = 0; i < td.rel_count; ++i) red_release_add(&p.counters[p.rels[td.rel_begin + i]], 1u);
-        if (p.trace_on) p.trace[t].stamp[S_END] = globaltimer();
+      } else if (!hand_over(t, sl.start_ticket, t_work)) {  // the releaser publishes it
+        record_error(p, E_PIPE_TIMEOUT, t);
+        ctl->fail = 1;
       }
       mbar_arrive(&ctl->slot_empty[slot.idx]);
     }
@@ -298,6 +335,10 @@ __global__ void __launch_bounds__(kThreads, 1) dag_exec_kernel(const __grid_cons
       mbar_init(&ctl->slot_full[s], 1);
       mbar_init(&ctl->slot_empty[s], 2);  // MMA warp + worker leader
     }
+    for (int s = 0; s < kRelSlots; ++s) {
+      mbar_init(&ctl->rel_full[s], 1);
+      mbar_init(&ctl->rel_empty[s], 1);
+    }
     mbar_fence_init();
     ctl->fail = 0;
   }
@@ -314,6 +355,9 @@ __global__ void __launch_bounds__(kThreads, 1) dag_exec_kernel(const __grid_cons
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) run_mma(p, smem, ctl);
+    __syncwarp();
+  } else if (warp == 2) {
+    if (lane == 0) run_releaser(p, ctl);
     __syncwarp();
   } else if (warp >= kWorkerBase / 32) {
     run_workers(p, smem, ctl, &ws);

@@ -51,6 +51,12 @@ struct TileSlot {
   uint64_t t_claim, t_start;
 };
 
+struct RelSlot {
+  int32_t t;             // finished queue position, or -1 = no more tiles
+  uint32_t start_ticket;
+  uint64_t t_work;
+};
+
 struct SmemCtl {
   uint64_t full[kStages];      // TMA -> MMA: stage filled
   uint64_t empty[kStages];     // MMA -> TMA: stage consumed
@@ -63,6 +69,9 @@ struct SmemCtl {
   uint64_t slot_full[kSlots];  // scheduler -> MMA, workers: slot published
   uint64_t slot_empty[kSlots]; // MMA + workers -> scheduler: slot consumed
   TileSlot slot[kSlots];
+  uint64_t rel_full[kRelSlots];   // workers -> releaser: tile finished
+  uint64_t rel_empty[kRelSlots];  // releaser -> workers: slot free
+  RelSlot rel[kRelSlots];
   uint32_t tmem_base;
   int32_t fail;                // CTA-local failure flag
   float bias[kMaxBN];          // bias slice of the GEMM tile in the epilogue
