@@ -153,7 +153,11 @@ def test_gemm_bf16_every_tile_width(bn, trans_b, out_dt):
 
 
 @pytest.mark.parametrize("N,dt_in,dt_out,scale", [(256, F32, BF16, 0.125), (1000, F32, F32, 1.0),
-                                                  (2048, BF16, F32, 0.5), (33, BF16, BF16, 2.0)])
+                                                  (2048, BF16, F32, 0.5), (33, BF16, BF16, 2.0),
+                                                  # vector path (N a multiple of 4, at most 256): both
+                                                  # halves of a lane's elements, one, and partial rows
+                                                  (128, BF16, BF16, 1.0), (252, F32, F32, 1.0),
+                                                  (4, F32, BF16, 1.0), (60, BF16, F32, 0.25), (132, F32, F32, 0.5)])
 def test_softmax(N, dt_in, dt_out, scale):
     w = Workload("softmax")
     x = w.buf(300, N, dt_in, "input", ("uniform", 5))
