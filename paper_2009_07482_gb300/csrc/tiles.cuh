@@ -748,17 +748,8 @@ __device__ __forceinline__ void softmax_rows_reg(const NodeParams &np, int r0, i
 // elements 4l..4l+3 and 128+4l..128+4l+3 of a row (vector loads and stores).
 // Each warp keeps R rows in registers and prefetches its next R rows while
 // it reduces, exponentiates and stores the current ones, so about
-// 2 x R x 1 KiB per warp are in flight (the tile is memory-latency bound).
-__device__ __forceinline__ void load4(const void *base, int dt, int64_t i, float (&v)[4]) {
-  if (dt == 0) {
-    const float4 a = __ldcg(reinterpret_cast<const float4 *>(static_cast<const float *>(base) + i));
-    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-  } else {
-    const uint2 a = __ldcg(reinterpret_cast<const uint2 *>(static_cast<const uint16_t *>(base) + i));
-    v[0] = __uint_as_float(a.x << 16); v[1] = __uint_as_float(a.x & 0xFFFF0000u);
-    v[2] = __uint_as_float(a.y << 16); v[3] = __uint_as_float(a.y & 0xFFFF0000u);
-  }
-}
+// 2 x R x 1 KiB per warp are in flight (the tile is memory-latency bound);
+// the R rows' max and sum reductions are interleaved.
 __device__ __forceinline__ void store4(void *base, int dt, int64_t i, const float (&v)[4]) {
   if (dt == 0) {
     *reinterpret_cast<float4 *>(static_cast<float *>(base) + i) = make_float4(v[0], v[1], v[2], v[3]);
@@ -769,76 +760,107 @@ __device__ __forceinline__ void store4(void *base, int dt, int64_t i, const floa
   }
 }
 
-template <int R>
+template <int R, int ADT>
 __device__ __forceinline__ void softmax_rows_vec256(const NodeParams &np, int r0, int r1, int stride) {
   const int lane = threadIdx.x & 31;
   const int N = np.N;
   const float s = np.scale;
-  const void *const A = np.A;
   void *const C = np.C;
-  const int a_dt = np.a_dt, c_dt = np.c_dt;
+  const int c_dt = np.c_dt;
   const int64_t lda = np.lda, ldc = np.ldc;
   // the two 4-element groups of this lane; a group is either wholly inside
   // the row or wholly outside (N is a multiple of 4)
   const int j0 = 4 * lane, j1 = 128 + 4 * lane;
   const bool g0 = j0 < N, g1 = j1 < N;
-  float x[R][8], y[R][8];
-  auto load_rows = [&](int rb, float (&z)[R][8]) {
+  // raw loaded bits stay untouched until the rows are computed, so the loads
+  // of the next rows remain in flight meanwhile
+  uint4 x[R][2], y[R][2];
+  auto load_rows = [&](int rb, uint4 (&z)[R][2]) {
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       const int r = rb + q * stride;
-      float a[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY}, b[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
-      if (r < r1 && g0) load4(A, a_dt, (int64_t)r * lda + j0, a);
-      if (r < r1 && g1) load4(A, a_dt, (int64_t)r * lda + j1, b);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        z[q][e] = (r < r1 && g0) ? s * a[e] : -INFINITY;
-        z[q][4 + e] = (r < r1 && g1) ? s * b[e] : -INFINITY;
+      z[q][0] = z[q][1] = make_uint4(0u, 0u, 0u, 0u);
+      if (r < r1) {
+        if (ADT == 0) {
+          const float *row = static_cast<const float *>(np.A) + (int64_t)r * lda;
+          if (g0) z[q][0] = __ldcg(reinterpret_cast<const uint4 *>(row + j0));
+          if (g1) z[q][1] = __ldcg(reinterpret_cast<const uint4 *>(row + j1));
+        } else {
+          const uint16_t *row = static_cast<const uint16_t *>(np.A) + (int64_t)r * lda;
+          if (g0) { const uint2 a = __ldcg(reinterpret_cast<const uint2 *>(row + j0)); z[q][0].x = a.x; z[q][0].y = a.y; }
+          if (g1) { const uint2 a = __ldcg(reinterpret_cast<const uint2 *>(row + j1)); z[q][1].x = a.x; z[q][1].y = a.y; }
+        }
       }
     }
+  };
+  auto value = [&](const uint4 &z, int e) -> float {
+    if (ADT == 0) return __uint_as_float(e == 0 ? z.x : e == 1 ? z.y : e == 2 ? z.z : z.w);
+    const uint32_t w = e < 2 ? z.x : z.y;
+    return __uint_as_float((e & 1) ? (w & 0xFFFF0000u) : (w << 16));
   };
   load_rows(r0, x);
   for (int rb = r0; rb < r1; rb += R * stride) {
     const int nb = rb + R * stride;
     if (nb < r1) load_rows(nb, y);  // prefetch the next rows
+    // all R rows at once: their reductions are independent shuffle chains
+    float v[R][8], m[R], sum[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      m[q] = -INFINITY;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        v[q][e] = g0 ? s * value(x[q][0], e) : -INFINITY;
+        v[q][4 + e] = g1 ? s * value(x[q][1], e) : -INFINITY;
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) m[q] = fmaxf(m[q], v[q][i]);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+      for (int q = 0; q < R; ++q) m[q] = fmaxf(m[q], __shfl_xor_sync(0xffffffffu, m[q], off));
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      sum[q] = 0.f;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        v[q][i] = ((i < 4 && g0) || (i >= 4 && g1)) ? expf(v[q][i] - m[q]) : 0.f;
+        sum[q] += v[q][i];
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+      for (int q = 0; q < R; ++q) sum[q] += __shfl_xor_sync(0xffffffffu, sum[q], off);
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       const int r = rb + q * stride;
       if (r >= r1) continue;
-      float m = -INFINITY;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) m = fmaxf(m, x[q][i]);
-      m = warp_max(m);
-      float sum = 0.f;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        x[q][i] = ((i < 4 && g0) || (i >= 4 && g1)) ? expf(x[q][i] - m) : 0.f;
-        sum += x[q][i];
-      }
-      sum = warp_sum(sum);
-      const float inv = 1.f / sum;
+      const float inv = 1.f / sum[q];
       float o0[4], o1[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        o0[e] = x[q][e] * inv;
-        o1[e] = x[q][4 + e] * inv;
+        o0[e] = v[q][e] * inv;
+        o1[e] = v[q][4 + e] * inv;
       }
       if (g0) store4(C, c_dt, (int64_t)r * ldc + j0, o0);
       if (g1) store4(C, c_dt, (int64_t)r * ldc + j1, o1);
     }
 #pragma unroll
-    for (int q = 0; q < R; ++q)
-#pragma unroll
-      for (int i = 0; i < 8; ++i) x[q][i] = y[q][i];
+    for (int q = 0; q < R; ++q) {
+      x[q][0] = y[q][0];
+      x[q][1] = y[q][1];
+    }
   }
 }
 
-__device__ __forceinline__ void tile_softmax(const TileDesc &t, const NodeParams &np) {
+__device__ __noinline__ void tile_softmax(const TileDesc &t, const NodeParams &np) {
   const int wid = (threadIdx.x - kWorkerBase) >> 5, lane = threadIdx.x & 31;
   constexpr int nw = kWorkers / 32;
   const int N = np.N;
   if (N <= 256 && np.vec && (N & 3) == 0) {
-    softmax_rows_vec256<4>(np, t.r0 + wid, t.r1, nw);
+    if (np.a_dt == 0) softmax_rows_vec256<4, 0>(np, t.r0 + wid, t.r1, nw);
+    else softmax_rows_vec256<4, 1>(np, t.r0 + wid, t.r1, nw);
   } else if (N <= 256) {
     softmax_rows_reg<8>(np, t.r0 + wid, t.r1, nw);
   } else if (N <= 1024) {
