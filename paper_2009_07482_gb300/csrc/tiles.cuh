@@ -824,7 +824,7 @@ __device__ __forceinline__ void softmax_rows_vec256(const NodeParams &np, int r0
       sum[q] = 0.f;
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        v[q][i] = ((i < 4 && g0) || (i >= 4 && g1)) ? expf(v[q][i] - m[q]) : 0.f;
+        v[q][i] = ((i < 4 && g0) || (i >= 4 && g1)) ? __expf(v[q][i] - m[q]) : 0.f;
         sum[q] += v[q][i];
       }
     }
