@@ -132,7 +132,9 @@ typedef struct {
   int32_t autotune;           /* 1: dag_create times candidate plans (tile widths x queue orders) on the
                                  device with zeroed buffers and keeps the fastest (see dag_plan_info) */
   int32_t f32_gemm;           /* dag_f32_gemm: how f32 GEMMs run */
-  int32_t reserved[4];
+  int32_t split_k;            /* 0: split the K loop of bf16 GEMMs whose depth level leaves most SMs idle
+                                 (up to 4 partials, summed in a fixed order); 1: never split */
+  int32_t reserved[3];
 } dag_options;
 
 /* f32 GEMM arithmetic.  DAG_F32_GEMM_TENSOR (default): on the tensor cores
@@ -435,11 +437,15 @@ dag_status dag_analyze(const dag_node_desc *nodes, int n_nodes, const dag_edge *
  * from one global counter after acquiring its inputs (start) and after
  * writing its output, before releasing it (end), %globaltimer times (ns) of
  * the claim of its queue position, the end of its waits, the start of its
- * epilogue / SIMT work and its release, and the SM it ran on. */
+ * epilogue / SIMT work and its release, and the SM it ran on.  A GEMM whose
+ * K loop is split (split != 0) has S tiles per output region, split =
+ * (s << 8) | S: partials s < S-1 write partial sums to scratch, and partial
+ * S-1 waits for them, adds them in order and writes the region. */
 typedef struct {
   int32_t node, r0, r1, c0, c1;   /* region of the kernel's output buffer */
   uint32_t start_ticket, end_ticket;
   uint32_t smid;
+  int32_t split, pad;
   uint64_t t_claim_ns, t_start_ns, t_work_ns, t_end_ns;
 } dag_trace_record;
 
@@ -471,7 +477,8 @@ dag_status dag_plan_get(dag_handle *h, dag_plan_info *out);
  * time model's, or node_cost_us as given; n = kernel count. */
 dag_status dag_node_costs_get(dag_handle *h, float *out, int cap, int *n);
 
-/* Per-tile static description in queue order: {node, r0, r1, c0, c1, cfg}. */
+/* Per-tile static description in queue order: {node, r0, r1, c0, c1,
+ * cfg | split << 16} (cfg: the tile shape code; split as in dag_trace_record). */
 dag_status dag_tiles_get(dag_handle *h, int32_t *out6, int cap, int *n);
 
 /* Host-only planning, no device needed: the tiles in queue order (as

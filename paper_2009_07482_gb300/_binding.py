@@ -47,7 +47,7 @@ class dag_edge(C.Structure):
 class dag_options(C.Structure):
     _fields_ = [("timeout_ns", u64), ("trace", i32), ("max_ctas", i32), ("scheduler", i32),
                 ("tile_override", i32), ("node_cost_us", C.POINTER(f32)), ("debug_never_ready", i32),
-                ("use_graph", i32), ("autotune", i32), ("f32_gemm", i32), ("reserved", i32 * 4)]
+                ("use_graph", i32), ("autotune", i32), ("f32_gemm", i32), ("split_k", i32), ("reserved", i32 * 3)]
 
 
 class dag_cq_options(C.Structure):
@@ -76,7 +76,8 @@ class dag_analysis(C.Structure):
 
 class dag_trace_record(C.Structure):
     _fields_ = [("node", i32), ("r0", i32), ("r1", i32), ("c0", i32), ("c1", i32), ("start_ticket", u32),
-                ("end_ticket", u32), ("smid", u32), ("t_claim_ns", u64), ("t_start_ns", u64), ("t_work_ns", u64), ("t_end_ns", u64)]
+                ("end_ticket", u32), ("smid", u32), ("split", i32), ("pad", i32), ("t_claim_ns", u64),
+                ("t_start_ns", u64), ("t_work_ns", u64), ("t_end_ns", u64)]
 
 
 class dag_plan_info(C.Structure):

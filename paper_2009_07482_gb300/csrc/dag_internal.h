@@ -55,9 +55,13 @@ struct TileDesc {
   int32_t cfg;    // bf16: BN; f32: F32Cfg; others: 0
   int32_t wait_begin, wait_count;  // into ExecParams::waits
   int32_t rel_begin, rel_count;    // into ExecParams::rels
-  int32_t pad;
+  int32_t split;  // split K: (s << 8) | S for partial s of S (the last one finishes the tile); 0 = whole K
 };
 static_assert(sizeof(TileDesc) == 48, "TileDesc layout");
+__host__ __device__ inline int split_count(const TileDesc &t) { return t.split & 0xFF; }
+__host__ __device__ inline int split_index(const TileDesc &t) { return t.split >> 8; }
+// a partial of a split tile that is not the last: it stores raw f32 partial sums
+__host__ __device__ inline bool split_partial(const TileDesc &t) { return t.split && split_index(t) < split_count(t) - 1; }
 
 // A dependency: counter[idx] must reach base(epoch) + target.  With
 // kWaitFlag set, idx is an input-buffer ready flag that must equal epoch+1.
@@ -66,6 +70,10 @@ struct Wait {
   uint32_t target;
 };
 constexpr uint32_t kWaitFlag = 0x80000000u;
+// With kWaitLate set, idx is a counter the workers wait on before the tile's
+// epilogue rather than the scheduler before its loads (a split-K tile's
+// finishing partial waits so for the other partials).
+constexpr uint32_t kWaitLate = 0x40000000u;
 
 struct NodeParams {
   const void *A, *B, *bias;
@@ -78,6 +86,7 @@ struct NodeParams {
   int32_t tmap_a, tmap_b;             // tensor-map indices (bf16 GEMM), else -1
   int32_t vec;                        // 16-byte vector paths are aligned
   int32_t tmap_c;                     // output tensor map for the TMA-store epilogue, else -1
+  float *scratch;                     // split K: partial sums, (S-1) blocks of 128 x BN f32 per output tile
 };
 
 struct Ctrl {

@@ -362,6 +362,8 @@ struct Plan {
   int n_sm = 148, grid = 148;
   std::vector<int> cfg;                 // per node tile config
   std::vector<char> tf32;               // per node: f32 GEMM on the tensor cores (3 x TF32)
+  std::vector<int> nsplit;              // per node: split-K factor S (0 = none)
+  bool allow_split = true;              // split K needs scratch memory (not in the no-alloc entry point)
   std::vector<TileDesc> tiles;          // node-major creation order
   std::vector<int> node_first, node_count;
   std::vector<TileDesc> queue;          // queue order (persistent mode)
@@ -386,7 +388,7 @@ static double tile_time_us(const Plan &P, int v, const TileDesc &t) {
   const double per_sm_bw = g_hbm_gbs * 1e9 / P.n_sm * 2.0;  // an SM alone streams faster than its fair share
   const double rows = t.r1 - t.r0, cols = t.c1 - t.c0;
   if (n.op == DAG_OP_GEMM) {
-    const double K = g.K[v];
+    const double K = (double)g.K[v] / (t.split ? split_count(t) : 1);
     const double flops = 2.0 * rows * cols * K;
     const int ea = esize(g.bufs[n.a].dtype);
     const double bytes = (rows + cols) * K * ea + rows * cols * esize(g.bufs[n.out].dtype);
@@ -470,6 +472,37 @@ static void choose_configs(Plan &P) {
   }
 }
 
+// Split K: a bf16 GEMM whose depth level leaves most SMs idle and whose K
+// loop is long is cut into S partials of K/S each (S <= 4, at least 16 K
+// blocks per partial), so that the level's tiles fill up to the SM count.
+// The last partial of each output tile adds the others' partial sums in a
+// fixed order, so the result does not depend on the schedule.
+static void choose_split(Plan &P) {
+  Graph &g = P.g;
+  const int nn = g.nn;
+  P.nsplit.assign(nn, 0);
+  if (!P.allow_split || P.opt.split_k == 1) return;
+  std::vector<int> depth(nn, 0);
+  for (int u : g.topo)
+    for (int v : g.succ[u]) depth[v] = std::max(depth[v], depth[u] + 1);
+  std::vector<long> level(nn + 1, 0);
+  for (int v = 0; v < nn; ++v) {
+    const dag_node_desc &n = g.nodes[v];
+    if (n.op != DAG_OP_GEMM) { level[depth[v]] += 8; continue; }
+    const int bn = g.bufs[n.a].dtype == DAG_BF16 ? P.cfg[v] : 64;
+    level[depth[v]] += ntiles_gemm(g, v, 128, std::max(bn, 64));
+  }
+  for (int v = 0; v < nn; ++v) {
+    const dag_node_desc &n = g.nodes[v];
+    if (n.op != DAG_OP_GEMM || g.bufs[n.a].dtype != DAG_BF16) continue;
+    const long lt = level[depth[v]];
+    const int kit = (g.K[v] + kBK - 1) / kBK;
+    if (lt * 2 > P.n_sm || kit < 32) continue;
+    const int S = std::min({4, (int)(P.n_sm / std::max(1L, lt)), kit / 16});
+    if (S >= 2) P.nsplit[v] = S;
+  }
+}
+
 // depth of every kernel in the kernel DAG (longest path from a root)
 static std::vector<int> depths(const Graph &g) {
   std::vector<int> d(g.nn, 0);
@@ -510,10 +543,16 @@ static void make_tiles(Plan &P) {
         bn = P.cfg[v] == F32_128x128 ? 128 : 64;
       }
       const int M = g.M[v], N = g.N[v];
-      for (int b = 0; b < n.batch; ++b)
-        for (int m = 0; m < M; m += bm)
-          for (int c = 0; c < N; c += bn)
-            push(op, b * M + m, b * M + std::min(m + bm, M), c, std::min(c + bn, N), P.cfg[v]);
+      const int S = P.nsplit.empty() ? 0 : P.nsplit[v];
+      // a split node: every output tile's partials 0..S-2 first, then the
+      // finishing partials (so a kernel-by-kernel launch can run them as two grids)
+      for (int s = S ? 0 : -1; s < (S ? S : 0); ++s)
+        for (int b = 0; b < n.batch; ++b)
+          for (int m = 0; m < M; m += bm)
+            for (int c = 0; c < N; c += bn) {
+              push(op, b * M + m, b * M + std::min(m + bm, M), c, std::min(c + bn, N), P.cfg[v]);
+              if (S) P.tiles.back().split = (s << 8) | S;
+            }
     } else if (n.op == DAG_OP_SOFTMAX) {
       // memory-bound and latency-bound per SM (a warp keeps two rows in
       // flight): 16..64 rows, split further while the level has fewer than
@@ -564,6 +603,7 @@ static void build_deps(Plan &P, std::vector<std::vector<int>> &tile_pred) {
   std::vector<int> gran(g.nb, 0), base(g.nb, -1), nblk(g.nb, 0);
   for (int i = 0; i < nt; ++i) {
     const TileDesc &t = P.tiles[i];
+    if (split_partial(t)) continue;  // partials write scratch, not the output
     const int root = g.root[g.nodes[t.node].out];
     const int rows = g.bufs[root].rows;
     int gg = gran[root] ? gran[root] : 128;
@@ -577,11 +617,36 @@ static void build_deps(Plan &P, std::vector<std::vector<int>> &tile_pred) {
       nblk[r] = (g.bufs[r].rows + gran[r] - 1) / gran[r];
       nc += nblk[r];
     }
+  // split K: one counter per output tile, released by its partials and
+  // waited on (S - 1 releases) by the partial that finishes the tile
+  std::vector<int> split_ctr(nt, -1);
+  {
+    std::vector<std::pair<std::pair<int, int64_t>, int>> fin;  // (node, r0 * 2^20 + c0) -> finishing tile
+    for (int i = 0; i < nt; ++i)
+      if (P.tiles[i].split && !split_partial(P.tiles[i])) {
+        split_ctr[i] = nc++;
+        fin.push_back({{P.tiles[i].node, (int64_t)P.tiles[i].r0 * (1 << 20) + P.tiles[i].c0}, i});
+      }
+    std::sort(fin.begin(), fin.end());
+    for (int i = 0; i < nt; ++i)
+      if (split_partial(P.tiles[i])) {
+        const std::pair<int, int64_t> key{P.tiles[i].node, (int64_t)P.tiles[i].r0 * (1 << 20) + P.tiles[i].c0};
+        auto it = std::lower_bound(fin.begin(), fin.end(), std::make_pair(key, -1));
+        split_ctr[i] = split_ctr[it->second];
+      }
+  }
   std::vector<uint32_t> target(nc, 0);
   std::vector<std::vector<int>> incr(nc);
   std::vector<std::vector<uint32_t>> rel_of(nt);
   for (int i = 0; i < nt; ++i) {
     const TileDesc &t = P.tiles[i];
+    if (split_partial(t)) {
+      const int c = split_ctr[i];
+      target[c]++;
+      incr[c].push_back(i);
+      rel_of[i].push_back((uint32_t)c);
+      continue;
+    }
     const int root = g.root[g.nodes[t.node].out];
     for (int b = t.r0 / gran[root]; b <= (t.r1 - 1) / gran[root]; ++b) {
       const int c = base[root] + b;
@@ -618,6 +683,11 @@ static void build_deps(Plan &P, std::vector<std::vector<int>> &tile_pred) {
         W.push_back(Wait{(uint32_t)c, target[c]});
         for (int u : incr[c]) tile_pred[i].push_back(u);
       }
+    }
+    if (t.split && !split_partial(t)) {  // the finishing partial waits for the others before its epilogue
+      const int c = split_ctr[i];
+      W.push_back(Wait{kWaitLate | (uint32_t)c, target[c]});
+      for (int u : incr[c]) tile_pred[i].push_back(u);
     }
     std::sort(W.begin(), W.end(), [](const Wait &a, const Wait &b) { return a.idx < b.idx; });
     W.erase(std::unique(W.begin(), W.end(), [](const Wait &a, const Wait &b) { return a.idx == b.idx; }), W.end());
@@ -760,6 +830,7 @@ static void roofline(Plan &P) {
 
 static void plan_tiles(Plan &P) {
   choose_configs(P);
+  choose_split(P);
   make_tiles(P);
   std::vector<std::vector<int>> tile_pred;
   build_deps(P, tile_pred);
@@ -785,7 +856,7 @@ extern "C" dag_status dag_plan_host(const dag_node_desc *nodes, int n_nodes, con
   *n_tiles = nt;
   for (int i = 0; out6 && i < nt && i < cap; ++i) {
     const TileDesc &t = P.queue[i];
-    const int32_t r[6] = {t.node, t.r0, t.r1, t.c0, t.c1, t.cfg};
+    const int32_t r[6] = {t.node, t.r0, t.r1, t.c0, t.c1, t.cfg | (t.split << 16)};
     memcpy(out6 + 6 * i, r, sizeof r);
   }
   if (info) {
@@ -811,6 +882,7 @@ struct dag_handle {
   // device memory
   void *arena = nullptr;      // buffers
   void *meta = nullptr;       // plan arrays
+  float *split_scratch = nullptr;  // split K partial sums
   std::vector<char *> dptr;   // per buffer (view-adjusted)
   std::vector<int64_t> ld;    // per buffer row pitch (elements)
   ExecParams xp{};            // persistent-mode parameters
@@ -851,6 +923,7 @@ static void free_handle(dag_handle *h) {
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->arena) cudaFree(h->arena);
   if (h->meta) cudaFree(h->meta);
+  if (h->split_scratch) cudaFree(h->split_scratch);
   for (auto &s : h->up)
     if (s) cudaStreamDestroy(s);
   if (h->down) cudaStreamDestroy(h->down);
@@ -992,6 +1065,26 @@ static dag_status create_impl(const dag_node_desc *nodes, int n_nodes, const dag
     vec &= ((size_t)g.coff[n.out] * esize(g.bufs[n.out].dtype)) % 16 == 0;
     q.vec = vec ? 1 : 0;
     if ((s = gemm_maps(P, v, q, maps))) { free_handle(h); return s; }
+  }
+  // split K scratch: (S - 1) blocks of 128 x BN f32 per output tile
+  {
+    std::vector<size_t> soff(nn, 0);
+    size_t stotal = 0;
+    for (int v = 0; v < nn; ++v)
+      if (P.nsplit[v] >= 2) {
+        soff[v] = stotal;
+        const int bn = P.cfg[v];
+        const size_t tiles = (size_t)g.nodes[v].batch * ((g.M[v] + kBM - 1) / kBM) * ((g.N[v] + bn - 1) / bn);
+        stotal += (size_t)(P.nsplit[v] - 1) * tiles * kBM * bn;
+      }
+    if (stotal) {
+      if (cudaMalloc(&h->split_scratch, stotal * sizeof(float)) != cudaSuccess) {
+        free_handle(h);
+        return fail(DAG_ENOMEM, "split-K scratch (%zu bytes)", stotal * sizeof(float));
+      }
+      for (int v = 0; v < nn; ++v)
+        if (P.nsplit[v] >= 2) np[v].scratch = h->split_scratch + soff[v];
+    }
   }
 
   // ---- plan arrays in one device block ----
@@ -1234,6 +1327,19 @@ extern "C" dag_status dag_submit(dag_handle *h, void *stream_) {
   return DAG_OK;
 }
 
+// One kernel's tiles as coarse grids (no waits inside a grid): a split node
+// runs its partials first and its finishing tiles in a second grid.
+static cudaError_t launch_node_coarse(const ExecParams &x, const Plan &P, int v, cudaStream_t st) {
+  const int first = P.node_first[v], count = P.node_count[v];
+  if (!count) return cudaSuccess;
+  int partials = 0;
+  while (partials < count && split_partial(P.tiles[first + partials])) ++partials;
+  cudaError_t e = cudaSuccess;
+  if (partials) e = launch_coarse(x, first, partials, st);
+  if (!e && count > partials) e = launch_coarse(x, first + partials, count - partials, st);
+  return e;
+}
+
 extern "C" dag_status dag_submit_coarse(dag_handle *h, void *stream_) {
   dag_status s = check_handle(h);
   if (s) return s;
@@ -1248,7 +1354,7 @@ extern "C" dag_status dag_submit_coarse(dag_handle *h, void *stream_) {
   x.tiles = h->d_coarse;
   if (P.opt.trace && P.tiles.size()) CUDA_TRY(cudaMemsetAsync(h->d_trace, 0, P.tiles.size() * sizeof(TraceRec), stream));
   for (int v : P.g.topo)
-    if (P.node_count[v]) CUDA_TRY(launch_coarse(x, P.node_first[v], P.node_count[v], stream));
+    CUDA_TRY(launch_node_coarse(x, P, v, stream));
   CUDA_TRY(cudaEventRecord(h->ev_done, stream));
   if ((s = enqueue_readbacks(h, stream))) return s;
   h->in_flight = true;
@@ -1375,7 +1481,8 @@ extern "C" dag_status dag_trace_get(dag_handle *h, dag_trace_record *out, int ca
   for (int i = 0; i < nt && i < cap; ++i) {
     const TileDesc &t = src[i];
     out[i] = dag_trace_record{t.node, t.r0, t.r1, t.c0, t.c1, tr[i].start_ticket, tr[i].end_ticket, tr[i].smid,
-                              tr[i].stamp[S_CLAIM], tr[i].stamp[S_READY], tr[i].stamp[S_WORK], tr[i].stamp[S_END]};
+                              t.split, 0, tr[i].stamp[S_CLAIM], tr[i].stamp[S_READY], tr[i].stamp[S_WORK],
+                              tr[i].stamp[S_END]};
   }
   return DAG_OK;
 }
@@ -1424,7 +1531,7 @@ extern "C" dag_status dag_tiles_get(dag_handle *h, int32_t *out6, int cap, int *
   *n = nt;
   for (int i = 0; out6 && i < nt && i < cap; ++i) {
     const TileDesc &t = h->P.queue[i];
-    const int32_t r[6] = {t.node, t.r0, t.r1, t.c0, t.c1, t.cfg};
+    const int32_t r[6] = {t.node, t.r0, t.r1, t.c0, t.c1, t.cfg | (t.split << 16)};
     memcpy(out6 + 6 * i, r, sizeof r);
   }
   return DAG_OK;
@@ -1449,6 +1556,7 @@ dag_status dagx::plan_into_region(const dag_node_desc *nodes, int n_nodes, const
   if (!P.opt.timeout_ns) P.opt.timeout_ns = 2000000000ull;
   P.opt.trace = 0;
   P.opt.debug_never_ready = 0;
+  P.allow_split = false;  // split K needs scratch memory
   // every input is already in the caller's device memory: no upload flags
   std::vector<dag_buffer_desc> bufs(buffers, buffers + std::max(0, n_buffers));
   for (auto &b : bufs)
@@ -1708,7 +1816,7 @@ extern "C" dag_status dag_submit_cq(dag_handle *h, const dag_cq_options *o, dag_
           if ((e = cudaStreamWaitEvent(q, h->cq_end[u], 0))) return e;
       // ndrange
       if ((e = cudaEventRecord(h->cq_beg[k], q))) return e;
-      if (P.node_count[k] && (e = launch_coarse(x, P.node_first[k], P.node_count[k], q))) return e;
+      if ((e = launch_node_coarse(x, P, k, q))) return e;
       if ((e = cudaEventRecord(h->cq_end[k], q))) return e;
       qof[k] = qi;
       processed[k] = 1;

@@ -37,6 +37,7 @@ static_assert(kSmemBytes <= 232448, "shared memory budget");
 struct WorkerShared {
   int32_t tile;
   int32_t ok;
+  uint32_t late_ticket;  // a split tile's finishing partial: start ticket after its late wait
 };
 
 __device__ __forceinline__ void record_error(const ExecParams &p, uint32_t code, int tile) {
@@ -51,6 +52,7 @@ __device__ __forceinline__ bool wait_deps(const ExecParams &p, const TileDesc &t
   for (int i = 0; i < t.wait_count; ++i) {
     const Wait w = p.waits[t.wait_begin + i];
     uint32_t spins = 0;
+    if (w.idx & kWaitLate) continue;  // taken by the workers before the epilogue
     if (w.idx & kWaitFlag) {
       const uint32_t *f = p.flags + (w.idx & ~kWaitFlag);
       while ((int32_t)(ld_acquire(f) - (epoch + 1u)) < 0) {
@@ -64,6 +66,23 @@ __device__ __forceinline__ bool wait_deps(const ExecParams &p, const TileDesc &t
         if ((++spins & 63u) == 0 && (globaltimer() > deadline || ld_relaxed(&p.ctrl->abort))) return false;
         __nanosleep(32);
       }
+    }
+  }
+  return true;
+}
+
+// The late waits of tile t (worker leader, before the epilogue).
+__device__ __forceinline__ bool wait_late(const ExecParams &p, const TileDesc &t, uint32_t epoch) {
+  const uint64_t deadline = globaltimer() + p.timeout_ns;
+  for (int i = 0; i < t.wait_count; ++i) {
+    const Wait w = p.waits[t.wait_begin + i];
+    if (!(w.idx & kWaitLate)) continue;
+    const uint32_t *c = p.counters + (w.idx & ~kWaitLate);
+    const uint32_t base = epoch * w.target;
+    uint32_t spins = 0;
+    while (ld_acquire(c) - base < w.target) {
+      if ((++spins & 63u) == 0 && (globaltimer() > deadline || ld_relaxed(&p.ctrl->abort))) return false;
+      __nanosleep(32);
     }
   }
   return true;
@@ -214,6 +233,7 @@ __device__ __forceinline__ void run_releaser(const ExecParams &p, SmemCtl *ctl) 
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void run_workers(const ExecParams &p, uint8_t *smem, SmemCtl *ctl, WorkerShared *ws) {
   const int wt = threadIdx.x - kWorkerBase;
+  const uint32_t epoch = p.mode == 0 ? ld_relaxed(&p.ctrl->epoch) : 0u;
   Ring slot = {0u, 0u};
   uint32_t accb = 0, ph[2] = {0u, 0u};
   Tf32State fs = {{0u, 0u}, 0u, 0u};  // the workers split f32 stages and add up their partials
@@ -259,12 +279,21 @@ __device__ __forceinline__ void run_workers(const ExecParams &p, uint8_t *smem, 
           worker_sync();
           if (p.trace_on && wt == 0) p.trace[t].stamp[S_ACC] = globaltimer();
         } else {
-          for (int kb = 0; kb < (np.K + kBK - 1) / kBK; ++kb) {  // the MMA issuer consumes these stages
+          int kb0, kb1;
+          gemm_krange(td, np, kb0, kb1);
+          for (int kb = kb0; kb < kb1; ++kb) {  // the MMA issuer consumes these stages
             fs.st.next(kStages);
             if (fs.st.idx == 0) ++fs.pass;
           }
           if (wt == 0) {
-            ws->ok = mbar_wait(&ctl->acc_full[accb], ph[accb], globaltimer() + p.timeout_ns) ? 1 : 0;
+            bool w = mbar_wait(&ctl->acc_full[accb], ph[accb], globaltimer() + p.timeout_ns);
+            // a split tile's finishing partial: the other partials' sums are in
+            // scratch; its start ticket is drawn after this last acquire
+            if (w && p.mode == 0 && td.split && !split_partial(td)) {
+              w = wait_late(p, td, epoch);
+              if (w && p.trace_on) ws->late_ticket = atomicAdd(&p.ctrl->ticket, 1u);
+            }
+            ws->ok = w ? 1 : 0;
             if (p.trace_on) p.trace[t].stamp[S_ACC] = globaltimer();
           }
           worker_sync();
@@ -298,7 +327,8 @@ __device__ __forceinline__ void run_workers(const ExecParams &p, uint8_t *smem, 
       if (!ok) {
         record_error(p, tc ? E_PIPE_TIMEOUT : E_BAD_TILE, t);
         ctl->fail = 1;
-      } else if (!hand_over(t, sl.start_ticket, t_work)) {  // the releaser publishes it
+      } else if (!hand_over(t, (td.split && !split_partial(td) && p.mode == 0) ? ws->late_ticket : sl.start_ticket,
+                            t_work)) {  // the releaser publishes it
         record_error(p, E_PIPE_TIMEOUT, t);
         ctl->fail = 1;
       }

@@ -110,18 +110,29 @@ __device__ __forceinline__ bool stage_wait_use(SmemCtl *ctl, uint32_t s, uint32_
 // box {64 (K), BN}; B MN-major: BN/64 boxes {64 (N), 64 (K)}.  All with the
 // 128-byte swizzle.
 // ---------------------------------------------------------------------------
+// K blocks [kb0, kb1) of a bf16 GEMM tile (a split tile's share of the K loop)
+__device__ __forceinline__ void gemm_krange(const TileDesc &t, const NodeParams &np, int &kb0, int &kb1) {
+  const int kiters = (np.K + kBK - 1) / kBK;
+  if (!t.split) { kb0 = 0; kb1 = kiters; return; }
+  const int S = split_count(t), s = split_index(t);
+  const int per = (kiters + S - 1) / S;
+  kb0 = min(kiters, s * per);
+  kb1 = min(kiters, kb0 + per);
+}
+
 __device__ __forceinline__ bool gemm_produce(const ExecParams &p, const TileDesc &t, const NodeParams &np,
                                              uint8_t *smem, SmemCtl *ctl, Ring &st, uint64_t deadline) {
   const int BN = t.cfg, M = np.M;
   const int bt = t.r0 / M, m0 = t.r0 - bt * M, n0 = t.c0;
-  const int kiters = (np.K + kBK - 1) / kBK;
+  int kb0, kiters;
+  gemm_krange(t, np, kb0, kiters);
   const CUtensorMap *ta = p.tmaps + np.tmap_a;
   const CUtensorMap *tb = p.tmaps + np.tmap_b;
   const int trans_b = np.trans_b;
   const uint32_t bytes = (uint32_t)(kStageA + BN * kBK * 2);
   uint8_t *sA = smem;
   uint8_t *sB = smem + kStages * kStageA;
-  for (int kb = 0; kb < kiters; ++kb) {
+  for (int kb = kb0; kb < kiters; ++kb) {
     if (!mbar_wait(&ctl->empty[st.idx], st.phase ^ 1u, deadline)) return false;
     uint64_t *bar = &ctl->full[st.idx];
     mbar_arrive_expect_tx(bar, bytes);
@@ -143,12 +154,13 @@ __device__ __forceinline__ bool gemm_produce(const ExecParams &p, const TileDesc
 __device__ __forceinline__ bool gemm_mma(const TileDesc &t, const NodeParams &np, uint8_t *smem, SmemCtl *ctl,
                                          Ring &st, uint32_t tmem_d, uint64_t deadline) {
   const int BN = t.cfg;
-  const int kiters = (np.K + kBK - 1) / kBK;
+  int kb0, kiters;
+  gemm_krange(t, np, kb0, kiters);
   const int trans_b = np.trans_b;
   const uint32_t idesc = idesc_bf16((uint32_t)BN, trans_b ? 0u : 1u);
   uint8_t *sA = smem;
   uint8_t *sB = smem + kStages * kStageA;
-  for (int kb = 0; kb < kiters; ++kb) {
+  for (int kb = kb0; kb < kiters; ++kb) {
     if (!mbar_wait(&ctl->full[st.idx], st.phase, deadline)) return false;
     tc_fence_after();
     const uint32_t a0 = smem_u32(sA + st.idx * kStageA);
@@ -161,7 +173,7 @@ __device__ __forceinline__ bool gemm_mma(const TileDesc &t, const NodeParams &np
       const uint64_t ad = smem_desc_sw128(a0 + kk * 32, 16, 1024);
       const uint64_t bd = trans_b ? smem_desc_sw128(b0 + kk * 32, 16, 1024)
                                   : smem_desc_sw128(b0 + kk * 2048, 64 * kBK * 2, 1024);
-      mma_bf16(tmem_d, ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
+      mma_bf16(tmem_d, ad, bd, idesc, (kb != kb0 || kk != 0) ? 1u : 0u);
     }
     mma_commit(&ctl->empty[st.idx]);
     st.next(kStages);
@@ -419,6 +431,44 @@ __device__ __forceinline__ void gemm_epilogue(const ExecParams &p, const TileDes
   const int half = wid >> 2;
   const int cw = BN / 2;
   const uint32_t trow = tmem_acc + ((uint32_t)(quad * 32) << 16);
+  // split K: this tile's scratch blocks (128 x BN f32 each, row-major)
+  const int S = split_count(t), sidx = split_index(t);
+  const float *parts = nullptr;
+  if (S) {
+    const int mt = (M + kBM - 1) / kBM, nt = (N + BN - 1) / BN;
+    const int64_t local = ((int64_t)bt * mt + m0 / kBM) * nt + n0 / BN;
+    parts = npg.scratch + local * (S - 1) * (int64_t)(kBM * BN);
+  }
+  const int trow_local = quad * 32 + lane;  // this thread's row in the tile
+  if (S && sidx < S - 1) {
+    // a partial: raw f32 sums to its scratch block
+    float *dst = const_cast<float *>(parts) + (int64_t)sidx * (kBM * BN) + (int64_t)trow_local * BN;
+    for (int c = half * cw; c < (half + 1) * cw; c += 32) {
+      float v[32];
+      tmem_ld32(trow + (uint32_t)c, v);
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        *reinterpret_cast<float4 *>(dst + c + 4 * j) = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+    }
+    return;
+  }
+  // the finishing partial adds the others' sums, in partial order, before its own
+  auto add_parts = [&](float (&v)[32], int c) {
+    if (!S) return;
+    float acc[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) acc[i] = 0.f;
+    for (int q = 0; q < S - 1; ++q) {
+      const float4 *src = reinterpret_cast<const float4 *>(parts + (int64_t)q * (kBM * BN) + (int64_t)trow_local * BN + c);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float4 x = __ldcg(src + j);
+        acc[4 * j] += x.x; acc[4 * j + 1] += x.y; acc[4 * j + 2] += x.z; acc[4 * j + 3] += x.w;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = acc[i] + v[i];
+  };
   if (tmap_c >= 0) {
     const CUtensorMap *mc = p.tmaps + tmap_c;
     uint8_t *stg = scratch + wid * (kEpiRows * 128);          // 4 KiB, 1024-aligned
@@ -432,6 +482,7 @@ __device__ __forceinline__ void gemm_epilogue(const ExecParams &p, const TileDes
       for (int sub = 0; sub < step; sub += 32) {
         float v[32];
         tmem_ld32(trow + (uint32_t)(c + sub), v);
+        add_parts(v, c + sub);
 #pragma unroll
         for (int i = 0; i < 32; ++i) v[i] = activate(act, fmaf(v[i], scale, ctl->bias[c + sub + i]));
         // 16-byte chunk j of this row goes to position j ^ (row % 8) (128-byte swizzle)
@@ -475,6 +526,7 @@ __device__ __forceinline__ void gemm_epilogue(const ExecParams &p, const TileDes
   for (int c = half * cw; c < (half + 1) * cw; c += 32) {
     float v[32];
     tmem_ld32(trow + (uint32_t)c, v);
+    add_parts(v, c);
     const int col = n0 + c;
     if (col >= N || !row_ok) continue;
 #pragma unroll

@@ -3,6 +3,7 @@ compare every computed buffer with the FP64 oracle."""
 import numpy as np
 
 import oracle
+from tests import trace_check
 from paper_2009_07482_gb300 import _binding as abi
 from paper_2009_07482_gb300.dag import Dag
 from synth import BF16, F32, storage_to_f64
@@ -51,11 +52,8 @@ def compare(w, got, ref_store, bids=None):
 
 def check_trace(w, d):
     recs = d.trace()
-    tiles = np.array([(r.node, r.r0, r.r1, r.c0, r.c1) for r in recs], np.int32)
-    start = np.array([r.start_ticket for r in recs], np.uint32)
-    end = np.array([r.end_ticket for r in recs], np.uint32)
-    rc, bu, bv = oracle.check_trace(w, tiles, start, end)
-    assert rc == 0, f"illegal trace: code {rc}, tiles {bu} -> {bv}"
+    trace_check.check(w, [(r.node, r.r0, r.r1, r.c0, r.c1) for r in recs], [r.split for r in recs],
+                      [r.start_ticket for r in recs], [r.end_ticket for r in recs])
     return recs
 
 

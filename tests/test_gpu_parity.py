@@ -266,3 +266,34 @@ def test_empty_and_degenerate_dags():
     d = Dag(w)
     d.run()
     d.close()
+
+
+SPLIT_CASES = [
+    dict(M=256, N=256, K=4096, dt=BF16),                                    # 8 tiles -> 4 partials each
+    dict(M=200, N=100, K=3000, dt=BF16, act="gelu", out_dt=BF16),           # ragged, 2 partials
+    dict(M=64, N=128, K=2048, dt=BF16, batch=2, trans_b=1, scale=0.5),     # batched, K-major B
+]
+
+
+@pytest.mark.parametrize("case", SPLIT_CASES, ids=lambda c: "-".join(f"{k}{v}" for k, v in c.items()))
+def test_gemm_split_k(case):
+    """A bf16 GEMM with few output tiles and a long K loop runs as split-K
+    partials; the finishing partial adds them in a fixed order, so results
+    are the same on every run, in both launch forms and on Alg. 1's streams."""
+    w = _gemm_case(**case)
+    d = Dag(w, options())
+    split = d.tiles()[:, 5] >> 16
+    assert (split > 0).any()
+    d.close()
+    _roundtrip(w)
+    ins = w.make_inputs()
+    d = Dag(w, options(max_ctas=3), resident_inputs=True)
+    d.set_inputs(ins)
+    d.run()
+    outs = {b: d.output(b) for b in sorted({n.out for n in w.nodes})}
+    d.run()
+    again = {b: d.output(b) for b in outs}
+    d.run_cq(n_queues=2, components=abi.DAG_TC_PER_KERNEL)
+    cq = {b: d.output(b) for b in outs}
+    d.close()
+    assert bits_equal(outs, again) and bits_equal(outs, cq)
