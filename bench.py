@@ -43,7 +43,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mlp_bf16",
-                    choices=["mlp_bf16", "mlp_f32", "fork_join", "encoder", "heads", "batched", "serving", "exp1"])
+                    choices=["mlp_bf16", "mlp_f32", "fork_join", "encoder", "heads", "softmax", "add", "batched",
+                             "serving", "exp1"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="batched: skip the cost-model comparison")
     ap.add_argument("--profile", action="store_true", help="few steps, no side measurements (for ncu)")
@@ -66,6 +67,25 @@ def make_workload(name):
         return branchy_mlp("f32"), "branchy MLP inference DAG, f32: batch 512, widths as mlp_bf16"
     if name == "fork_join":
         return fork_join(256), "fork-join DAG (paper Fig. 1): 3 GEMMs 256^3 f32 + add"
+    if name == "softmax":
+        from synth.workloads import Workload
+        w = Workload("attention_softmax_level")
+        for h in range(16):
+            a = w.buf(2048, 256, "f32", "input", ("uniform", 100 + h), f"S{h}")
+            w.node("softmax", a, w.buf(2048, 256, "bf16", "output", name=f"P{h}"), scale=0.125, name=f"softmax{h}")
+        return w, ("the encoder's attention softmax level alone: 16 heads x (8 x 256) rows x 256, f32 scores in, "
+                   "bf16 out, scale 1/8 (memory-bound)")
+    if name == "add":
+        from synth.workloads import Workload
+        w = Workload("add_tree_4096")
+        xs = [w.buf(4096, 4096, "bf16", "input", ("uniform", 200 + i), f"X{i}") for i in range(4)]
+        s0 = w.buf(4096, 4096, "bf16", name="S0")
+        s1 = w.buf(4096, 4096, "bf16", name="S1")
+        w.node("add", xs[0], s0, b=xs[1], name="add0")
+        w.node("add", xs[2], s1, b=xs[3], name="add1")
+        w.node("add", s0, w.buf(4096, 4096, "bf16", "output", name="Y"), b=s1, name="add2")
+        return w, ("a two-level add tree ((X0+X1)+(X2+X3)) of 4096 x 4096 bf16 matrices, 32 MiB each, "
+                   "larger than L2 together (memory-bound)")
     if name == "heads":
         from synth.workloads import transformer_heads
         return transformer_heads(16, 256), ("the paper's transformer-layer DAG (§6): 16 heads, beta = 256, f32; "
@@ -226,6 +246,23 @@ def oracle_model(workload, ra=4, rb=12):
         w = fork_join(256)
         t = _oracle_seconds(w, w.make_inputs(), repeat=3)
         return t, "fork-join 256^3 f32: the whole DAG, mean of 3 runs", (w, 256, t, 0.0)
+    if workload == "softmax":
+        from synth.workloads import Workload
+        w = Workload("one_head_softmax")
+        a = w.buf(2048, 256, "f32", "input", ("uniform", 100), "S0")
+        w.node("softmax", a, w.buf(2048, 256, "bf16", "output"), scale=0.125)
+        t = _oracle_seconds(w, w.make_inputs(_INPUTS))
+        return 16 * t, f"softmax level: 1 of 16 heads ({t:.2f} s), times 16", (w, 1, t, 0.0)
+    if workload == "add":
+        from synth.workloads import Workload
+        w = Workload("add_tree_rows")
+        xs = [w.buf(256, 4096, "bf16", "input", ("uniform", 200 + i)) for i in range(4)]
+        s0, s1 = w.buf(256, 4096, "bf16"), w.buf(256, 4096, "bf16")
+        w.node("add", xs[0], s0, b=xs[1])
+        w.node("add", xs[2], s1, b=xs[3])
+        w.node("add", s0, w.buf(256, 4096, "bf16", "output"), b=s1)
+        t = _oracle_seconds(w, w.make_inputs(_INPUTS))
+        return 16 * t, f"add tree: 256 of 4096 rows ({t:.2f} s), times 16", (w, 1, t, 0.0)
     if workload == "heads":
         from synth.workloads import transformer_heads
         w = transformer_heads(1, 256)
@@ -290,7 +327,7 @@ def run_reference(args):
             t = t + (scale_rows - rows) * slope
         elif args.workload == "encoder":
             t = 8 * t
-        elif args.workload == "heads":
+        elif args.workload in ("heads", "softmax", "add"):
             t = 16 * t
         if i >= args.warmup:
             per.append(t)
@@ -680,14 +717,21 @@ def main():
     src_bf16 = f"{peaks_src} bf16 burst (MEASURED_PEAKS.json)" if peaks_src == "measured" else "fallback 1.9 PF/s"
     src_f32 = ("3 x TF32 on the tensor cores: measured bf16 burst x 1.1/2.25 (nominal tf32/bf16) / 3"
                if f32_peak == tc_peak else "derived: 152 SMs x 128 f32 FMA/clk x 2 flop x max SM clock")
-    if fl["f32"] == 0:
+    if fl["f32"] == 0 and fl["bf16"] == 0:  # no GEMM: the DAG is bound by HBM bandwidth
+        roof = {"bound": "hbm", "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "peak_source": f"{peaks_src} HBM copy bandwidth (MEASURED_PEAKS.json)"}
+    elif fl["f32"] == 0:
         roof = {"bound": "tensor", "peak": peaks["bf16_tflops"], "peak_source": src_bf16}
     elif fl["bf16"] == 0:
         roof = {"bound": "alu" if args.f32_simt else "tensor", "peak": f32_peak, "peak_source": src_f32}
     else:
         roof = {"bound": "tensor", "peak": info.flops / t_bound_us / 1e6,
                 "peak_source": f"flop-weighted: bf16 at {src_bf16}, f32 at {src_f32}"}
-    roof.update({"achieved": achieved, "unit": "TFLOP/s", "frac": achieved / roof["peak"]})
+    if roof["bound"] == "hbm":
+        achieved = info.bytes / (mean_us * 1e-6) / 1e9
+        roof.update({"achieved": achieved, "frac": achieved / roof["peak"]})
+    else:
+        roof.update({"achieved": achieved, "unit": "TFLOP/s", "frac": achieved / roof["peak"]})
     bf16 = fl["bf16"] > 0 and fl["f32"] == 0
     traffic, sha = traffic_for(args.workload)
     roof["traffic"] = traffic
@@ -698,7 +742,9 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mean_us / 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16" if bf16 else ("f32" if fl["bf16"] == 0 else "bf16+f32"),
+        "vs_baseline": None,
+        "dtype": ("f32+bf16 (no GEMM)" if roof["bound"] == "hbm" else "bf16" if bf16
+                  else ("f32" if fl["bf16"] == 0 else "bf16+f32")),
         "data": "synthetic (seeded SplitMix64)",
         "config": {"workload": desc, "dags_per_step": n_dags, "nodes": len(w.nodes), "tiles": info.n_tiles,
                    "grid": info.grid,

@@ -562,11 +562,11 @@ static void make_tiles(Plan &P) {
       while (rows > 16 && (double)((R + rows - 1) / rows) < share) rows /= 2;
       for (int r = 0; r < R; r += rows) push(T_SOFTMAX, r, std::min(r + rows, R), 0, C, 0);
     } else {
-      // at most 32K and at least 4K elements per tile, split further while
+      // at most 64K and at least 4K elements per tile, split further while
       // the level has fewer than its share of two tiles per SM
       const double share = 1.0 * P.n_sm * ((double)R * C) / std::max(1.0, level_elems[dep[v]]);
       int rows = 256;
-      while (rows > 1 && (long)rows * C > 32768) rows /= 2;
+      while (rows > 1 && (long)rows * C > 65536) rows /= 2;
       while (rows > 1 && (double)((R + rows - 1) / rows) < share && (long)(rows / 2) * C >= 4096) rows /= 2;
       for (int r = 0; r < R; r += rows)
         push(n.op == DAG_OP_ADD ? T_ADD : T_UNARY, r, std::min(r + rows, R), 0, C, 0);
