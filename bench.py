@@ -10,6 +10,8 @@ write) between timed steps, outside the timed events.
 
 Also measured and reported on the same JSON line:
   coarse     the same tiles launched kernel by kernel on one stream
+  epilogue_fusion  the persistent executor with the opt-in epilogue fusion
+             modes, when the DAG has kernels they would fuse
   e2e        the same metric through the C ABI with host buffers: upload of X
              from pinned memory, execution, readback of Y, every step
   roofline   the executor kernel's achieved TFLOP/s against the measured peak
@@ -585,7 +587,7 @@ def main():
     torch.cuda.set_device(local)
     from paper_2009_07482_gb300 import _binding as abi
     from paper_2009_07482_gb300 import build as libbuild
-    from paper_2009_07482_gb300.dag import Dag, options
+    from paper_2009_07482_gb300.dag import Dag, describe, options
     libbuild.build()
     abi.dag_set_device(local)
     peaks, peaks_src = load_peaks()
@@ -608,8 +610,9 @@ def main():
     X_ids = [i for i in w.input_ids() if i not in weights]
     Y_ids = w.output_ids()
 
-    def make_dag(streamed):
-        o = options(use_graph=1 if batched else 0, f32_gemm=abi.DAG_F32_GEMM_SIMT if args.f32_simt else 0)
+    def make_dag(streamed, fuse=0):
+        o = options(use_graph=1 if batched else 0, f32_gemm=abi.DAG_F32_GEMM_SIMT if args.f32_simt else 0,
+                    fuse=fuse)
         if batched:
             return Dag.batch(wl, o, resident_inputs=not streamed, streamed=set(X_ids) if streamed else None)
         return Dag(w, o, streamed=set(X_ids)) if streamed else Dag(w, o, resident_inputs=True)
@@ -629,10 +632,11 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    def timed(submit, steps, warmup):
+    def timed(submit, steps, warmup, dd=None):
+        dd = dd or d
         for _ in range(warmup):
             submit(sp)
-            abi.check(d.wait(), "wait")
+            abi.check(dd.wait(), "wait")
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         barrier()
         t0 = time.perf_counter()
@@ -641,7 +645,7 @@ def main():
             a.record(stream)
             submit(sp)
             b.record(stream)
-            abi.check(d.wait(), "wait")
+            abi.check(dd.wait(), "wait")
         barrier()
         wall = time.perf_counter() - t0
         return [a.elapsed_time(b) * 1e3 for a, b in evs], wall  # us
@@ -654,7 +658,24 @@ def main():
         d.close()
         return 0
     coarse_us, _ = timed(d.submit_coarse, max(3, args.steps // 4) if batched else max(10, args.steps // 4), 3)
-    n_coarse_launches = sum(1 for _ in w.nodes)
+    # kernel-by-kernel launches: one per kernel not fused into a GEMM, two for a split GEMM
+    fused = d.fusion()
+    tl = d.tiles()
+    split_nodes = {int(t[0]) for t in tl if (int(t[5]) >> 16) & 0xFF}
+    n_coarse_launches = sum(1 + (v in split_nodes) for v in range(len(w.nodes)) if fused[v] < 0)
+    # the opt-in epilogue-fusion modes (the measured line runs without fusion)
+    unfused = None
+    for name, mode in (("activations", abi.DAG_FUSE_ACT), ("activations_and_adds", abi.DAG_FUSE_ALL)):
+        n_f = sum(h >= 0 for h in abi.dag_fusion_host(*describe(w, resident_inputs=True), options(fuse=mode)))
+        if not n_f:
+            continue
+        u = make_dag(False, fuse=mode)
+        u.set_inputs(ins)
+        u.run()
+        u_us, _ = timed(u.submit, max(5, args.steps // 2), 3, u)
+        unfused = unfused or {"mode": "none"}
+        unfused[name] = {"fused_kernels": int(n_f), "median_us": statistics.median(u_us)}
+        u.close()
     alg1 = None if batched else paper_alg1(d, abi, reps=8)
 
     # max over ranks of the mean step time
@@ -765,6 +786,8 @@ def main():
     if alg1:
         alg1["speedup_persistent_over_best"] = alg1["best_us"] / med
         line["paper_alg1"] = alg1
+    if unfused:
+        line["epilogue_fusion"] = unfused
     if batched and not args.no_learned:
         def timed_fn(dd, n):
             out = []

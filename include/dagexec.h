@@ -134,8 +134,21 @@ typedef struct {
   int32_t f32_gemm;           /* dag_f32_gemm: how f32 GEMMs run */
   int32_t split_k;            /* 0: split the K loop of bf16 GEMMs whose depth level leaves most SMs idle
                                  (up to 4 partials, summed in a fixed order); 1: never split */
-  int32_t reserved[3];
+  int32_t fuse;               /* dag_fuse: elementwise kernels run inside the epilogue of the tensor-core
+                                 GEMM whose output they read, when that output has no other reader, is no
+                                 view and no DAG input or output (up to 2 in a chain per GEMM; each step is
+                                 rounded to its buffer's dtype exactly as if stored: bit-identical results) */
+  int32_t reserved[2];
 } dag_options;
+
+/* Epilogue fusion (dag_options.fuse).  DAG_FUSE_NONE (default): every kernel
+ * runs its own tiles.  DAG_FUSE_ACT: activation kernels run in the epilogue
+ * of their GEMM.  DAG_FUSE_ALL: adds as well; the epilogue then waits for the
+ * add's other operand and reads it row by row through L2.  A plan with fused
+ * kernels runs a second build of the executor kernel that holds the fused
+ * epilogue code; its higher register pressure slows every other tile of the
+ * launch, which is why fusion is off unless asked for. */
+typedef enum { DAG_FUSE_NONE = 0, DAG_FUSE_ACT = 1, DAG_FUSE_ALL = 2 } dag_fuse;
 
 /* f32 GEMM arithmetic.  DAG_F32_GEMM_TENSOR (default): on the tensor cores
  * with the 3 x TF32 split (each operand x = hi + lo, hi = tf32(x),
@@ -200,7 +213,9 @@ dag_status dag_submit(dag_handle *h, void *stream);
 
 /* dag_submit_coarse: the coarse-grained baseline: uploads on `stream`, then
  * one launch per kernel in topological order on `stream` (the same tile code,
- * a grid of that kernel's tiles, no cross-kernel overlap), then readbacks. */
+ * a grid of that kernel's tiles, no cross-kernel overlap), then readbacks.
+ * A GEMM with fused elementwise kernels launches in the place of the last of
+ * them (DAG_FUSE_NONE gives one launch per kernel throughout). */
 dag_status dag_submit_coarse(dag_handle *h, void *stream);
 
 /*
@@ -215,7 +230,9 @@ dag_status dag_submit_coarse(dag_handle *h, void *stream);
  *     (the command queues Q): the uploads of its isolated inputs, then its
  *     launch (a grid of the kernel's tiles, as in dag_submit_coarse), then the
  *     readback of its output if registered; a predecessor on another stream
- *     is waited on through its event (the set E_Q);
+ *     is waited on through its event (the set E_Q); a GEMM with fused
+ *     elementwise kernels launches in the turn of the last of them, and the
+ *     turns before it launch nothing (their events still order successors);
  *   callbacks: after each kernel of END(T), a host function (the paper's cb)
  *     marks it finished; when all of END(T) have, T is finished, its ready
  *     successor components enter F and the device is returned.
@@ -440,7 +457,10 @@ dag_status dag_analyze(const dag_node_desc *nodes, int n_nodes, const dag_edge *
  * epilogue / SIMT work and its release, and the SM it ran on.  A GEMM whose
  * K loop is split (split != 0) has S tiles per output region, split =
  * (s << 8) | S: partials s < S-1 write partial sums to scratch, and partial
- * S-1 waits for them, adds them in order and writes the region. */
+ * S-1 waits for them, adds them in order and writes the region.  A GEMM tile
+ * with fused elementwise kernels (dag_fusion_get) carries the GEMM's id and
+ * region and writes the last fused kernel's output there; like a finishing
+ * partial, its start ticket is drawn after the waits of its epilogue. */
 typedef struct {
   int32_t node, r0, r1, c0, c1;   /* region of the kernel's output buffer */
   uint32_t start_ticket, end_ticket;
@@ -480,6 +500,18 @@ dag_status dag_node_costs_get(dag_handle *h, float *out, int cap, int *n);
 /* Per-tile static description in queue order: {node, r0, r1, c0, c1,
  * cfg | split << 16} (cfg: the tile shape code; split as in dag_trace_record). */
 dag_status dag_tiles_get(dag_handle *h, int32_t *out6, int cap, int *n);
+
+/* Epilogue fusion of the plan (see dag_options.fuse): out[v] = the GEMM
+ * kernel whose tiles compute kernel v, or -1 when v runs its own tiles;
+ * n = kernel count.  A fused kernel's buffer between the GEMM and it is never
+ * written; the GEMM's tiles write the last fused kernel's output, and their
+ * trace records carry the GEMM's id. */
+dag_status dag_fusion_get(dag_handle *h, int32_t *out, int cap, int *n);
+
+/* Host-only: the fusion dag_create would choose (as dag_fusion_get), n_nodes
+ * entries in out. */
+dag_status dag_fusion_host(const dag_node_desc *nodes, int n_nodes, const dag_edge *edges, int n_edges,
+                           const dag_buffer_desc *buffers, int n_buffers, const dag_options *opts, int32_t *out);
 
 /* Host-only planning, no device needed: the tiles in queue order (as
  * dag_tiles_get) that dag_create would build for a GPU with n_sm SMs running

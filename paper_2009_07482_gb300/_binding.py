@@ -27,6 +27,7 @@ DAG_ACT_NONE, DAG_ACT_RELU, DAG_ACT_GELU = 0, 1, 2
 DAG_BUF_INPUT, DAG_BUF_OUTPUT, DAG_BUF_RESIDENT = 1, 2, 4
 DAG_SCHED_RANK_MODEL, DAG_SCHED_RANK_GIVEN, DAG_SCHED_FIFO = 0, 1, 2
 DAG_F32_GEMM_TENSOR, DAG_F32_GEMM_SIMT = 0, 1
+DAG_FUSE_NONE, DAG_FUSE_ACT, DAG_FUSE_ALL = 0, 1, 2
 DAG_TC_GIVEN, DAG_TC_WHOLE, DAG_TC_PER_KERNEL = 0, 1, 2
 
 
@@ -47,7 +48,8 @@ class dag_edge(C.Structure):
 class dag_options(C.Structure):
     _fields_ = [("timeout_ns", u64), ("trace", i32), ("max_ctas", i32), ("scheduler", i32),
                 ("tile_override", i32), ("node_cost_us", C.POINTER(f32)), ("debug_never_ready", i32),
-                ("use_graph", i32), ("autotune", i32), ("f32_gemm", i32), ("split_k", i32), ("reserved", i32 * 3)]
+                ("use_graph", i32), ("autotune", i32), ("f32_gemm", i32), ("split_k", i32), ("fuse", i32),
+                ("reserved", i32 * 2)]
 
 
 class dag_cq_options(C.Structure):
@@ -134,6 +136,9 @@ _SIGS = {
     "dag_plan_host": (i32, [C.POINTER(dag_node_desc), C.c_int, C.POINTER(dag_edge), C.c_int,
                             C.POINTER(dag_buffer_desc), C.c_int, C.POINTER(dag_options), C.c_int,
                             C.POINTER(i32), C.c_int, C.POINTER(C.c_int), C.POINTER(dag_plan_info)]),
+    "dag_fusion_get": (i32, [C.c_void_p, C.POINTER(i32), C.c_int, C.POINTER(C.c_int)]),
+    "dag_fusion_host": (i32, [C.POINTER(dag_node_desc), C.c_int, C.POINTER(dag_edge), C.c_int,
+                              C.POINTER(dag_buffer_desc), C.c_int, C.POINTER(dag_options), C.POINTER(i32)]),
     "dag_set_peaks": (None, [C.c_double, C.c_double, C.c_double]),
     "dag_set_device": (i32, [C.c_int]),
     "dag_trace_stamps": (i32, [C.c_void_p, C.POINTER(u64), C.c_int, C.POINTER(C.c_int)]),
@@ -248,6 +253,25 @@ def dag_plan_host(nodes, edges, buffers, options: Optional[dag_options] = None, 
     check(lib().dag_plan_host(na, nn, ea, ne, ba, nb, opt, n_sm, out, n.value, C.byref(n), None), "dag_plan_host")
     import numpy as np
     return np.frombuffer(out, dtype=np.int32)[: 6 * n.value].reshape(-1, 6).copy(), info
+
+
+def dag_fusion_host(nodes, edges, buffers, options: Optional[dag_options] = None):
+    """Per kernel: the GEMM whose epilogue computes it, or -1 (see dag_fusion_get)."""
+    na, nn = _arr(dag_node_desc, nodes)
+    ea, ne = _arr(dag_edge, edges)
+    ba, nb = _arr(dag_buffer_desc, buffers)
+    out = (i32 * max(1, nn))()
+    check(lib().dag_fusion_host(na, nn, ea, ne, ba, nb, C.byref(options) if options else None, out),
+          "dag_fusion_host")
+    return list(out[:nn])
+
+
+def dag_fusion_get(h):
+    n = C.c_int(0)
+    check(lib().dag_fusion_get(h, None, 0, C.byref(n)), "dag_fusion_get")
+    out = (i32 * max(1, n.value))()
+    check(lib().dag_fusion_get(h, out, n.value, C.byref(n)), "dag_fusion_get")
+    return list(out[:n.value])
 
 
 def dag_set_input(h, buf: int, host_ptr) -> None:

@@ -122,7 +122,9 @@ def model_tile_us(w) -> np.ndarray:
 
 
 def node_costs_from_tile_times(tile_us: Sequence[float], counts: Sequence[int], grid: int) -> List[float]:
-    return [float(t) * math.ceil(max(1, c) / grid) for t, c in zip(tile_us, counts)]
+    """Tile time x waves; 0 for a kernel with no tiles of its own (computed in
+    the epilogue of the GEMM it is fused into)."""
+    return [float(t) * math.ceil(c / grid) if c else 0.0 for t, c in zip(tile_us, counts)]
 
 
 def profile_costs(w, inputs, opts=None) -> List[float]:

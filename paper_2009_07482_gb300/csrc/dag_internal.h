@@ -46,6 +46,7 @@ constexpr int kSlots = 2;                     // scheduler -> MMA / workers tile
 constexpr int kRelSlots = 4;                  // workers -> releaser ring of finished tiles
 constexpr int kWorkerScratch = 32 * 1024;     // per-CTA worker scratch: epilogue staging / f32 tiles
 constexpr int kEpiRows = 32;                  // epilogue store box: 32 rows x 128 bytes per warp
+constexpr int kMaxPost = 2;                   // elementwise kernels fused into one GEMM epilogue
 
 struct TileDesc {
   int32_t node;   // kernel id
@@ -72,8 +73,22 @@ struct Wait {
 constexpr uint32_t kWaitFlag = 0x80000000u;
 // With kWaitLate set, idx is a counter the workers wait on before the tile's
 // epilogue rather than the scheduler before its loads (a split-K tile's
-// finishing partial waits so for the other partials).
+// finishing partial waits so for the other partials, and a GEMM tile with
+// fused elementwise kernels for their other operands).
 constexpr uint32_t kWaitLate = 0x40000000u;
+
+// An elementwise kernel fused into a GEMM epilogue: out = act(v + X) for an
+// add (X its other operand, same rows and columns as the GEMM output), or
+// act(v) for an activation; v is the previous step's value rounded to the
+// dtype that step's kernel stores.
+struct PostOp {
+  const void *X;    // add: the other operand (view-adjusted); activation: null
+  int64_t ldx;      // X row pitch (elements)
+  int32_t x_dt;     // 0 = f32, 1 = bf16
+  int32_t act;      // dag_act
+  int32_t out_dt;   // dtype this kernel's output is stored in
+  int32_t xvec;     // X rows start on 16-byte boundaries
+};
 
 struct NodeParams {
   const void *A, *B, *bias;
@@ -87,6 +102,10 @@ struct NodeParams {
   int32_t vec;                        // 16-byte vector paths are aligned
   int32_t tmap_c;                     // output tensor map for the TMA-store epilogue, else -1
   float *scratch;                     // split K: partial sums, (S-1) blocks of 128 x BN f32 per output tile
+  int32_t n_post;                     // elementwise kernels fused into the epilogue (C, ldc, c_dt and
+                                      // tmap_c then describe the last one's output)
+  int32_t o_dt;                       // dtype of the GEMM's own output (rounding point before post[0])
+  PostOp post[kMaxPost];
 };
 
 struct Ctrl {
@@ -128,6 +147,8 @@ struct ExecParams {
   int32_t mode;        // 0 = persistent queue, 1 = coarse (one tile per CTA, no waits)
   int32_t tile_begin;  // coarse: first tile of this launch
   int32_t trace_on;
+  int32_t fused;       // some GEMM epilogue runs fused elementwise kernels (selects the kernel variant)
+  int32_t pad_;
   const Wait *waits;
   const uint32_t *rels;
   const NodeParams *nodes;

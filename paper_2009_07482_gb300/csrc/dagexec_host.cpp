@@ -363,6 +363,8 @@ struct Plan {
   std::vector<int> cfg;                 // per node tile config
   std::vector<char> tf32;               // per node: f32 GEMM on the tensor cores (3 x TF32)
   std::vector<int> nsplit;              // per node: split-K factor S (0 = none)
+  std::vector<int> absorbed_by;         // per node: the GEMM whose epilogue computes it, or -1
+  std::vector<std::vector<int>> post;   // per GEMM: elementwise kernels fused into its epilogue, in order
   bool allow_split = true;              // split K needs scratch memory (not in the no-alloc entry point)
   std::vector<TileDesc> tiles;          // node-major creation order
   std::vector<int> node_first, node_count;
@@ -379,6 +381,11 @@ struct Plan {
 };
 
 static int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// the buffer kernel v's tiles write: a GEMM with fused kernels writes the last one's output
+static int tile_out(const Plan &P, int v) {
+  return P.post.empty() || P.post[v].empty() ? P.g.nodes[v].out : P.g.nodes[P.post[v].back()].out;
+}
 
 // per-tile time model (us): roofline of the tile's work on one SM plus a
 // fixed per-tile overhead
@@ -472,6 +479,48 @@ static void choose_configs(Plan &P) {
   }
 }
 
+// Epilogue fusion (DAG_FUSE_ACT, DAG_FUSE_ALL): an activation kernel (with
+// DAG_FUSE_ALL also an add) reading the output O of a tensor-core GEMM runs
+// inside that GEMM's epilogue when no other kernel reads O, O is a plain
+// buffer (not a view, none into it) and neither a DAG input nor output, and
+// the kernel is not fused elsewhere; its own output may continue the chain,
+// up to kMaxPost kernels.  O is then never written: the epilogue rounds each
+// step to the dtype of the buffer it stands for, so the values are those of
+// the unfused DAG.  An add's other operand is waited for before the epilogue
+// (a late wait), not before the K loop.
+static void choose_fusion(Plan &P) {
+  Graph &g = P.g;
+  P.absorbed_by.assign(g.nn, -1);
+  P.post.assign(g.nn, {});
+  if (P.opt.fuse != DAG_FUSE_ACT && P.opt.fuse != DAG_FUSE_ALL) return;
+  std::vector<int> views(g.nb, 0);
+  for (int b = 0; b < g.nb; ++b)
+    if (g.root[b] != b) views[g.root[b]]++;
+  auto private_out = [&](int v) {  // read by exactly one kernel, and only by it
+    const int o = g.nodes[v].out;
+    return g.root[o] == o && !views[o] && !(g.bufs[o].flags & (DAG_BUF_INPUT | DAG_BUF_OUTPUT)) &&
+           g.succ[v].size() == 1;
+  };
+  for (int v : g.topo) {
+    const dag_node_desc &n = g.nodes[v];
+    if (n.op != DAG_OP_GEMM || !(g.bufs[n.a].dtype == DAG_BF16 || P.tf32[v])) continue;
+    int cur = v;
+    while ((int)P.post[v].size() < kMaxPost && private_out(cur)) {
+      const int e = g.succ[cur][0], o = g.nodes[cur].out;
+      const dag_node_desc &m = g.nodes[e];
+      if (P.absorbed_by[e] >= 0) break;
+      if (m.op == DAG_OP_ADD) {
+        if (P.opt.fuse != DAG_FUSE_ALL || (m.a == o) == (m.b == o)) break;  // reads O exactly once
+      } else if (m.op != DAG_OP_UNARY || m.a != o) {
+        break;
+      }
+      P.absorbed_by[e] = v;
+      P.post[v].push_back(e);
+      cur = e;
+    }
+  }
+}
+
 // Split K: a bf16 GEMM whose depth level leaves most SMs idle and whose K
 // loop is long is cut into S partials of K/S each (S <= 4, at least 16 K
 // blocks per partial), so that the level's tiles fill up to the SM count.
@@ -488,7 +537,10 @@ static void choose_split(Plan &P) {
   std::vector<long> level(nn + 1, 0);
   for (int v = 0; v < nn; ++v) {
     const dag_node_desc &n = g.nodes[v];
-    if (n.op != DAG_OP_GEMM) { level[depth[v]] += 8; continue; }
+    if (n.op != DAG_OP_GEMM) {
+      if (P.absorbed_by[v] < 0) level[depth[v]] += 8;
+      continue;
+    }
     const int bn = g.bufs[n.a].dtype == DAG_BF16 ? P.cfg[v] : 64;
     level[depth[v]] += ntiles_gemm(g, v, 128, std::max(bn, 64));
   }
@@ -519,7 +571,7 @@ static void make_tiles(Plan &P) {
   const std::vector<int> dep = depths(g);
   std::vector<double> level_elems(g.nn + 1, 0.0);
   for (int v = 0; v < g.nn; ++v)
-    if (g.nodes[v].op != DAG_OP_GEMM)
+    if (g.nodes[v].op != DAG_OP_GEMM && P.absorbed_by[v] < 0)
       level_elems[dep[v]] += (double)g.bufs[g.nodes[v].out].rows * g.bufs[g.nodes[v].out].cols;
   P.node_first.assign(g.nn, 0);
   P.node_count.assign(g.nn, 0);
@@ -532,7 +584,9 @@ static void make_tiles(Plan &P) {
       P.tiles.push_back(t);
     };
     const int R = g.bufs[n.out].rows, C = g.bufs[n.out].cols;
-    if (n.op == DAG_OP_GEMM) {
+    if (P.absorbed_by[v] >= 0) {
+      // computed by its GEMM's tiles
+    } else if (n.op == DAG_OP_GEMM) {
       const bool bf = g.bufs[n.a].dtype == DAG_BF16;
       const int op = bf ? T_GEMM_BF16 : P.tf32[v] ? T_GEMM_TF32 : T_GEMM_F32;
       int bm, bn;
@@ -563,11 +617,15 @@ static void make_tiles(Plan &P) {
       for (int r = 0; r < R; r += rows) push(T_SOFTMAX, r, std::min(r + rows, R), 0, C, 0);
     } else {
       // at most 64K and at least 4K elements per tile, split further while
-      // the level has fewer than its share of two tiles per SM
+      // the level's memory-bound kernels still fit in one tile per SM (their
+      // share of the SMs by elements): a tile's fixed cost -- dependency
+      // hand-off, one L2 round trip, release -- exceeds its transfer time, so
+      // one wave of larger tiles beats two waves of smaller ones
       const double share = 1.0 * P.n_sm * ((double)R * C) / std::max(1.0, level_elems[dep[v]]);
       int rows = 256;
       while (rows > 1 && (long)rows * C > 65536) rows /= 2;
-      while (rows > 1 && (double)((R + rows - 1) / rows) < share && (long)(rows / 2) * C >= 4096) rows /= 2;
+      while (rows > 1 && (double)((R + rows / 2 - 1) / (rows / 2)) <= share && (long)(rows / 2) * C >= 4096)
+        rows /= 2;
       for (int r = 0; r < R; r += rows)
         push(n.op == DAG_OP_ADD ? T_ADD : T_UNARY, r, std::min(r + rows, R), 0, C, 0);
     }
@@ -604,7 +662,7 @@ static void build_deps(Plan &P, std::vector<std::vector<int>> &tile_pred) {
   for (int i = 0; i < nt; ++i) {
     const TileDesc &t = P.tiles[i];
     if (split_partial(t)) continue;  // partials write scratch, not the output
-    const int root = g.root[g.nodes[t.node].out];
+    const int root = g.root[tile_out(P, t.node)];
     const int rows = g.bufs[root].rows;
     int gg = gran[root] ? gran[root] : 128;
     while (gg > 16 && ((t.r0 % gg) || ((t.r1 % gg) && t.r1 != rows))) gg /= 2;
@@ -647,7 +705,7 @@ static void build_deps(Plan &P, std::vector<std::vector<int>> &tile_pred) {
       rel_of[i].push_back((uint32_t)c);
       continue;
     }
-    const int root = g.root[g.nodes[t.node].out];
+    const int root = g.root[tile_out(P, t.node)];
     for (int b = t.r0 / gran[root]; b <= (t.r1 - 1) / gran[root]; ++b) {
       const int c = base[root] + b;
       target[c]++;
@@ -689,6 +747,25 @@ static void build_deps(Plan &P, std::vector<std::vector<int>> &tile_pred) {
       W.push_back(Wait{kWaitLate | (uint32_t)c, target[c]});
       for (int u : incr[c]) tile_pred[i].push_back(u);
     }
+    int prev = g.nodes[t.node].out;
+    if (!split_partial(t))  // fused adds: their other operand's rows, before the epilogue
+      for (int e : P.post[t.node]) {
+        const dag_node_desc &m = g.nodes[e];
+        const int x = m.a == prev ? m.b : m.a;
+        prev = m.out;
+        if (m.op != DAG_OP_ADD) continue;
+        const int root = g.root[x];
+        if (P.flag_of_root[root] >= 0) {
+          W.push_back(Wait{kWaitFlag | (uint32_t)P.flag_of_root[root], 1u});
+          continue;
+        }
+        if (!gran[root]) continue;  // resident input
+        for (int b = t.r0 / gran[root]; b <= (t.r1 - 1) / gran[root]; ++b) {
+          const int c = base[root] + b;
+          W.push_back(Wait{kWaitLate | (uint32_t)c, target[c]});
+          for (int u : incr[c]) tile_pred[i].push_back(u);
+        }
+      }
     std::sort(W.begin(), W.end(), [](const Wait &a, const Wait &b) { return a.idx < b.idx; });
     W.erase(std::unique(W.begin(), W.end(), [](const Wait &a, const Wait &b) { return a.idx == b.idx; }), W.end());
     std::sort(tile_pred[i].begin(), tile_pred[i].end());
@@ -770,7 +847,9 @@ static void order_tiles(Plan &P, const std::vector<std::vector<int>> &tile_pred)
     }
     const int t = avail.top();
     avail.pop();
-    const double start = std::max(now, workers.top());
+    // a tile that became available at a later `now` (when no worker was
+    // free earlier) still cannot start before its inputs are ready
+    const double start = std::max(std::max(now, workers.top()), ready_t[t]);
     workers.pop();
     const double fin = start + est[t];
     workers.push(fin);
@@ -830,6 +909,7 @@ static void roofline(Plan &P) {
 
 static void plan_tiles(Plan &P) {
   choose_configs(P);
+  choose_fusion(P);
   choose_split(P);
   make_tiles(P);
   std::vector<std::vector<int>> tile_pred;
@@ -996,6 +1076,52 @@ static dag_status gemm_maps(const Plan &P, int v, NodeParams &q, std::vector<CUt
   return DAG_OK;
 }
 
+// Kernel parameters of node v over the view-adjusted device buffers dptr /
+// ld, the elementwise kernels fused into its epilogue, and its tensor maps.
+static dag_status fill_params(const Plan &P, int v, char *const *dptr, const int64_t *ld, NodeParams &q,
+                              std::vector<CUtensorMap> &maps) {
+  const Graph &g = P.g;
+  const dag_node_desc &n = g.nodes[v];
+  memset(&q, 0, sizeof q);
+  q.A = dptr[n.a];
+  q.lda = ld[n.a];
+  q.a_dt = g.bufs[n.a].dtype;
+  if (n.op == DAG_OP_GEMM || n.op == DAG_OP_ADD) { q.B = dptr[n.b]; q.ldb = ld[n.b]; q.b_dt = g.bufs[n.b].dtype; }
+  if (n.op == DAG_OP_GEMM && n.bias >= 0) { q.bias = dptr[n.bias]; q.bias_dt = g.bufs[n.bias].dtype; }
+  const int out = tile_out(P, v);
+  q.C = dptr[out];
+  q.ldc = ld[out];
+  q.c_dt = g.bufs[out].dtype;
+  q.o_dt = g.bufs[n.out].dtype;
+  q.M = g.M[v]; q.N = g.N[v]; q.K = g.K[v]; q.batch = n.op == DAG_OP_GEMM ? n.batch : 1;
+  q.trans_b = n.trans_b; q.act = n.act; q.scale = n.scale;
+  q.tmap_a = q.tmap_b = q.tmap_c = -1;
+  // 16-byte vector paths: every operand starts on a 16-byte boundary (row
+  // pitches are multiples of 16 bytes)
+  bool vec = true;
+  int in[3];
+  const int k = g.inputs(v, in);
+  for (int i = 0; i < k; ++i) vec &= ((uintptr_t)dptr[in[i]] % 16) == 0;
+  vec &= ((uintptr_t)dptr[out] % 16) == 0;
+  q.vec = vec ? 1 : 0;
+  int prev = n.out;
+  for (int e : P.post[v]) {
+    const dag_node_desc &m = g.nodes[e];
+    PostOp &o = q.post[q.n_post++];
+    o.act = m.act;
+    o.out_dt = g.bufs[m.out].dtype;
+    if (m.op == DAG_OP_ADD) {
+      const int x = m.a == prev ? m.b : m.a;
+      o.X = dptr[x];
+      o.ldx = ld[x];
+      o.x_dt = g.bufs[x].dtype;
+      o.xvec = ((uintptr_t)dptr[x] % 16) == 0 && (ld[x] * esize(o.x_dt)) % 16 == 0;
+    }
+    prev = m.out;
+  }
+  return gemm_maps(P, v, q, maps);
+}
+
 static dag_status create_impl(const dag_node_desc *nodes, int n_nodes, const dag_edge *edges, int n_edges,
                               const dag_buffer_desc *buffers, int n_buffers, const dag_options *opts,
                               dag_handle **out) {
@@ -1041,31 +1167,8 @@ static dag_status create_impl(const dag_node_desc *nodes, int n_nodes, const dag
   const int nn = g.nn, nt = (int)P.tiles.size();
   std::vector<NodeParams> np(std::max(1, nn));
   std::vector<CUtensorMap> maps;
-  for (int v = 0; v < nn; ++v) {
-    const dag_node_desc &n = g.nodes[v];
-    NodeParams &q = np[v];
-    memset(&q, 0, sizeof q);
-    q.A = h->dptr[n.a];
-    q.lda = h->ld[n.a];
-    q.a_dt = g.bufs[n.a].dtype;
-    if (n.op == DAG_OP_GEMM || n.op == DAG_OP_ADD) { q.B = h->dptr[n.b]; q.ldb = h->ld[n.b]; q.b_dt = g.bufs[n.b].dtype; }
-    if (n.op == DAG_OP_GEMM && n.bias >= 0) { q.bias = h->dptr[n.bias]; q.bias_dt = g.bufs[n.bias].dtype; }
-    q.C = h->dptr[n.out];
-    q.ldc = h->ld[n.out];
-    q.c_dt = g.bufs[n.out].dtype;
-    q.M = g.M[v]; q.N = g.N[v]; q.K = g.K[v]; q.batch = n.op == DAG_OP_GEMM ? n.batch : 1;
-    q.trans_b = n.trans_b; q.act = n.act; q.scale = n.scale;
-    q.tmap_a = q.tmap_b = q.tmap_c = -1;
-    // 16-byte vector paths: every operand's view offset is 16-byte aligned
-    // (row pitches are multiples of 16 elements by construction)
-    bool vec = true;
-    int in[3];
-    const int k = g.inputs(v, in);
-    for (int i = 0; i < k; ++i) vec &= ((size_t)g.coff[in[i]] * esize(g.bufs[in[i]].dtype)) % 16 == 0;
-    vec &= ((size_t)g.coff[n.out] * esize(g.bufs[n.out].dtype)) % 16 == 0;
-    q.vec = vec ? 1 : 0;
-    if ((s = gemm_maps(P, v, q, maps))) { free_handle(h); return s; }
-  }
+  for (int v = 0; v < nn; ++v)
+    if ((s = fill_params(P, v, h->dptr.data(), h->ld.data(), np[v], maps))) { free_handle(h); return s; }
   // split K scratch: (S - 1) blocks of 128 x BN f32 per output tile
   {
     std::vector<size_t> soff(nn, 0);
@@ -1116,6 +1219,7 @@ static dag_status create_impl(const dag_node_desc *nodes, int n_nodes, const dag
   x.mode = 0;
   x.tile_begin = 0;
   x.trace_on = P.opt.trace ? 1 : 0;
+  x.fused = std::any_of(P.post.begin(), P.post.end(), [](const std::vector<int> &c) { return !c.empty(); }) ? 1 : 0;
   x.waits = (const Wait *)(m + o_waits);
   x.rels = (const uint32_t *)(m + o_rels);
   x.nodes = (const NodeParams *)(m + o_nodes);
@@ -1340,6 +1444,15 @@ static cudaError_t launch_node_coarse(const ExecParams &x, const Plan &P, int v,
   return e;
 }
 
+// The kernel whose tiles launch in kernel v's turn of a kernel-by-kernel
+// order (-1: none): a GEMM with fused kernels launches in the last one's turn,
+// when every operand of the chain has been produced.
+static int launch_in_turn(const Plan &P, int v) {
+  const int head = P.absorbed_by[v];
+  if (head >= 0) return P.post[head].back() == v ? head : -1;
+  return P.post[v].empty() ? v : -1;
+}
+
 extern "C" dag_status dag_submit_coarse(dag_handle *h, void *stream_) {
   dag_status s = check_handle(h);
   if (s) return s;
@@ -1354,7 +1467,7 @@ extern "C" dag_status dag_submit_coarse(dag_handle *h, void *stream_) {
   x.tiles = h->d_coarse;
   if (P.opt.trace && P.tiles.size()) CUDA_TRY(cudaMemsetAsync(h->d_trace, 0, P.tiles.size() * sizeof(TraceRec), stream));
   for (int v : P.g.topo)
-    CUDA_TRY(launch_node_coarse(x, P, v, stream));
+    if (launch_in_turn(P, v) >= 0) CUDA_TRY(launch_node_coarse(x, P, launch_in_turn(P, v), stream));
   CUDA_TRY(cudaEventRecord(h->ev_done, stream));
   if ((s = enqueue_readbacks(h, stream))) return s;
   h->in_flight = true;
@@ -1542,6 +1655,29 @@ extern "C" dag_status dag_tiles_get(dag_handle *h, int32_t *out6, int cap, int *
 // the entry point that allocates nothing (noalloc.cu): the region is a
 // file-scope device array there, the buffers belong to the caller.
 // ---------------------------------------------------------------------------
+extern "C" dag_status dag_fusion_get(dag_handle *h, int32_t *out, int cap, int *n) {
+  dag_status s = check_handle(h);
+  if (s) return s;
+  if (!n) return fail(DAG_EINVAL, "null n");
+  *n = h->P.g.nn;
+  for (int v = 0; out && v < h->P.g.nn && v < cap; ++v) out[v] = h->P.absorbed_by[v];
+  return DAG_OK;
+}
+
+extern "C" dag_status dag_fusion_host(const dag_node_desc *nodes, int n_nodes, const dag_edge *edges, int n_edges,
+                                      const dag_buffer_desc *buffers, int n_buffers, const dag_options *opts,
+                                      int32_t *out) {
+  if (!out && n_nodes > 0) return fail(DAG_EINVAL, "null output array");
+  Plan P;
+  if (opts) P.opt = *opts;
+  dag_status s = build_graph(nodes, n_nodes, edges, n_edges, buffers, n_buffers, P.g);
+  if (s) return s;
+  choose_configs(P);
+  choose_fusion(P);
+  for (int v = 0; v < P.g.nn; ++v) out[v] = P.absorbed_by[v];
+  return DAG_OK;
+}
+
 dag_status dagx::report_error(dag_status s, const char *msg) { return fail(s, "%s", msg); }
 
 dag_status dagx::plan_into_region(const dag_node_desc *nodes, int n_nodes, const dag_buffer_desc *buffers,
@@ -1587,29 +1723,8 @@ dag_status dagx::plan_into_region(const dag_node_desc *nodes, int n_nodes, const
   const int nn = g.nn, nt = (int)P.queue.size();
   std::vector<NodeParams> np(std::max(1, nn));
   std::vector<CUtensorMap> maps;
-  for (int v = 0; v < nn; ++v) {
-    const dag_node_desc &n = g.nodes[v];
-    NodeParams &q = np[v];
-    memset(&q, 0, sizeof q);
-    q.A = dptr[n.a];
-    q.lda = ld[n.a];
-    q.a_dt = g.bufs[n.a].dtype;
-    if (n.op == DAG_OP_GEMM || n.op == DAG_OP_ADD) { q.B = dptr[n.b]; q.ldb = ld[n.b]; q.b_dt = g.bufs[n.b].dtype; }
-    if (n.op == DAG_OP_GEMM && n.bias >= 0) { q.bias = dptr[n.bias]; q.bias_dt = g.bufs[n.bias].dtype; }
-    q.C = dptr[n.out];
-    q.ldc = ld[n.out];
-    q.c_dt = g.bufs[n.out].dtype;
-    q.M = g.M[v]; q.N = g.N[v]; q.K = g.K[v]; q.batch = n.op == DAG_OP_GEMM ? n.batch : 1;
-    q.trans_b = n.trans_b; q.act = n.act; q.scale = n.scale;
-    q.tmap_a = q.tmap_b = q.tmap_c = -1;
-    bool vec = true;
-    int in[3];
-    const int k = g.inputs(v, in);
-    for (int i = 0; i < k; ++i) vec &= ((uintptr_t)dptr[in[i]] % 16) == 0;
-    vec &= ((uintptr_t)dptr[n.out] % 16) == 0;
-    q.vec = vec ? 1 : 0;
-    if ((s = gemm_maps(P, v, q, maps))) return s;
-  }
+  for (int v = 0; v < nn; ++v)
+    if ((s = fill_params(P, v, dptr.data(), ld.data(), np[v], maps))) return s;
   // layout inside the region; counters, flags and control block start at zero
   size_t o_maps = 0;
   size_t o_tiles = align_up(o_maps + maps.size() * sizeof(CUtensorMap), 256);
@@ -1642,6 +1757,7 @@ dag_status dagx::plan_into_region(const dag_node_desc *nodes, int n_nodes, const
   xp.ctrl = (Ctrl *)(region + o_ctrl);
   xp.trace = nullptr;
   xp.trace_on = 0;
+  xp.fused = std::any_of(P.post.begin(), P.post.end(), [](const std::vector<int> &c) { return !c.empty(); }) ? 1 : 0;
   xp.timeout_ns = P.opt.timeout_ns;
   return DAG_OK;
 }
@@ -1816,7 +1932,7 @@ extern "C" dag_status dag_submit_cq(dag_handle *h, const dag_cq_options *o, dag_
           if ((e = cudaStreamWaitEvent(q, h->cq_end[u], 0))) return e;
       // ndrange
       if ((e = cudaEventRecord(h->cq_beg[k], q))) return e;
-      if ((e = launch_node_coarse(x, P, k, q))) return e;
+      if (launch_in_turn(P, k) >= 0 && (e = launch_node_coarse(x, P, launch_in_turn(P, k), q))) return e;
       if ((e = cudaEventRecord(h->cq_end[k], q))) return e;
       qof[k] = qi;
       processed[k] = 1;

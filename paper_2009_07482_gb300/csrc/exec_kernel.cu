@@ -37,7 +37,7 @@ static_assert(kSmemBytes <= 232448, "shared memory budget");
 struct WorkerShared {
   int32_t tile;
   int32_t ok;
-  uint32_t late_ticket;  // a split tile's finishing partial: start ticket after its late wait
+  uint32_t late_ticket;  // a tile with waits before its epilogue: start ticket drawn after them
 };
 
 __device__ __forceinline__ void record_error(const ExecParams &p, uint32_t code, int tile) {
@@ -231,6 +231,7 @@ __device__ __forceinline__ void run_releaser(const ExecParams &p, SmemCtl *ctl) 
 // workers (256 threads); every decision is taken by the leader and broadcast
 // through shared memory, so all workers reach the same named barriers
 // ---------------------------------------------------------------------------
+template <bool kFused>
 __device__ __forceinline__ void run_workers(const ExecParams &p, uint8_t *smem, SmemCtl *ctl, WorkerShared *ws) {
   const int wt = threadIdx.x - kWorkerBase;
   const uint32_t epoch = p.mode == 0 ? ld_relaxed(&p.ctrl->epoch) : 0u;
@@ -267,6 +268,13 @@ __device__ __forceinline__ void run_workers(const ExecParams &p, uint8_t *smem, 
     const uint64_t t_work = (p.trace_on && wt == 0) ? globaltimer() : 0;
     const TileDesc td = p.tiles[t];
     const NodeParams &np = p.nodes[td.node];
+    // waits taken before the epilogue: a split tile's finishing partial (the
+    // other partials' sums) and a tile with fused adds (their other operands);
+    // its start ticket is drawn after them
+    // (the plain variant keeps the split-only form, so its code is unchanged)
+    const bool late = kFused ? p.mode == 0 && (td.op == T_GEMM_BF16 || td.op == T_GEMM_TF32) && !split_partial(td) &&
+                                   (td.split || np.n_post)
+                             : td.split && !split_partial(td) && p.mode == 0;
     bool ok = true;
     switch (td.op) {
       case T_GEMM_BF16:
@@ -277,6 +285,13 @@ __device__ __forceinline__ void run_workers(const ExecParams &p, uint8_t *smem, 
           const bool mine = tf32_worker_loop(np, smem, ctl, fs, acc, globaltimer() + p.timeout_ns);
           if (!mine) ws->ok = 0;  // any warp that timed out fails the tile
           worker_sync();
+          if (kFused && late) {
+            if (wt == 0 && ws->ok) {
+              if (!wait_late(p, td, epoch)) ws->ok = 0;
+              else if (p.trace_on) ws->late_ticket = atomicAdd(&p.ctrl->ticket, 1u);
+            }
+            worker_sync();
+          }
           if (p.trace_on && wt == 0) p.trace[t].stamp[S_ACC] = globaltimer();
         } else {
           int kb0, kb1;
@@ -287,9 +302,7 @@ __device__ __forceinline__ void run_workers(const ExecParams &p, uint8_t *smem, 
           }
           if (wt == 0) {
             bool w = mbar_wait(&ctl->acc_full[accb], ph[accb], globaltimer() + p.timeout_ns);
-            // a split tile's finishing partial: the other partials' sums are in
-            // scratch; its start ticket is drawn after this last acquire
-            if (w && p.mode == 0 && td.split && !split_partial(td)) {
+            if (w && late) {
               w = wait_late(p, td, epoch);
               if (w && p.trace_on) ws->late_ticket = atomicAdd(&p.ctrl->ticket, 1u);
             }
@@ -302,7 +315,8 @@ __device__ __forceinline__ void run_workers(const ExecParams &p, uint8_t *smem, 
         ok = ws->ok != 0;
         if (ok) {
           tc_fence_after();
-          gemm_epilogue(p, td, np, ctl, ctl->tmem_base + accb * kAccCols, smem + kSmemStages);
+          if (kFused && np.n_post) gemm_epilogue<true>(p, td, np, ctl, ctl->tmem_base + accb * kAccCols, smem + kSmemStages);
+          else gemm_epilogue<false>(p, td, np, ctl, ctl->tmem_base + accb * kAccCols, smem + kSmemStages);
         }
         tc_fence_before();
         break;
@@ -327,8 +341,7 @@ __device__ __forceinline__ void run_workers(const ExecParams &p, uint8_t *smem, 
       if (!ok) {
         record_error(p, tc ? E_PIPE_TIMEOUT : E_BAD_TILE, t);
         ctl->fail = 1;
-      } else if (!hand_over(t, (td.split && !split_partial(td) && p.mode == 0) ? ws->late_ticket : sl.start_ticket,
-                            t_work)) {  // the releaser publishes it
+      } else if (!hand_over(t, late ? ws->late_ticket : sl.start_ticket, t_work)) {  // the releaser publishes it
         record_error(p, E_PIPE_TIMEOUT, t);
         ctl->fail = 1;
       }
@@ -339,6 +352,10 @@ __device__ __forceinline__ void run_workers(const ExecParams &p, uint8_t *smem, 
   }
 }
 
+// kFused: some GEMM of the plan runs fused elementwise kernels in its
+// epilogue; the plain variant is compiled without that code, so that its
+// register allocation does not pay for it.
+template <bool kFused>
 __global__ void __launch_bounds__(kThreads, 1) dag_exec_kernel(const __grid_constant__ ExecParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -390,7 +407,7 @@ __global__ void __launch_bounds__(kThreads, 1) dag_exec_kernel(const __grid_cons
     if (lane == 0) run_releaser(p, ctl);
     __syncwarp();
   } else if (warp >= kWorkerBase / 32) {
-    run_workers(p, smem, ctl, &ws);
+    run_workers<kFused>(p, smem, ctl, &ws);
   }
 
   // teardown: free TMEM; the last CTA of a persistent launch rewinds the queue
@@ -416,12 +433,14 @@ __global__ void __launch_bounds__(kThreads, 1) dag_exec_kernel(const __grid_cons
 int exec_smem_bytes() { return kSmemBytes; }
 
 cudaError_t exec_prepare() {
-  return cudaFuncSetAttribute(dag_exec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  const cudaError_t e = cudaFuncSetAttribute(dag_exec_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kSmemBytes);
+  return e ? e : cudaFuncSetAttribute(dag_exec_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
 }
 
 int max_coresident_ctas_per_sm() {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dag_exec_kernel, kThreads, kSmemBytes) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dag_exec_kernel<false>, kThreads, kSmemBytes) != cudaSuccess)
     return 0;
   return n;
 }
@@ -430,7 +449,8 @@ cudaError_t launch_persistent(const ExecParams &p, int grid, cudaStream_t s) {
   ExecParams q = p;
   q.mode = 0;
   q.tile_begin = 0;
-  dag_exec_kernel<<<grid, kThreads, kSmemBytes, s>>>(q);
+  if (q.fused) dag_exec_kernel<true><<<grid, kThreads, kSmemBytes, s>>>(q);
+  else dag_exec_kernel<false><<<grid, kThreads, kSmemBytes, s>>>(q);
   return cudaGetLastError();
 }
 
@@ -438,7 +458,8 @@ cudaError_t launch_coarse(const ExecParams &p, int tile_begin, int n, cudaStream
   ExecParams q = p;
   q.mode = 1;
   q.tile_begin = tile_begin;
-  dag_exec_kernel<<<n, kThreads, kSmemBytes, s>>>(q);
+  if (q.fused) dag_exec_kernel<true><<<n, kThreads, kSmemBytes, s>>>(q);
+  else dag_exec_kernel<false><<<n, kThreads, kSmemBytes, s>>>(q);
   return cudaGetLastError();
 }
 

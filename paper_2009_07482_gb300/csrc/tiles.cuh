@@ -409,13 +409,77 @@ __device__ __forceinline__ bool tf32_worker_loop(const NodeParams &np, uint8_t *
   return ok;
 }
 
+// Elementwise kernels fused into a GEMM epilogue, on 32 consecutive values of
+// one output row (row grow, columns col..col+31): each step first rounds the
+// value to the dtype of the buffer the previous kernel would have stored,
+// then applies act(v + X) (an add; X read through L2, written by other SMs in
+// this launch) or act(v) -- the arithmetic of the elementwise tile itself.
+__device__ __forceinline__ float round_dt(int dt, float x) { return dt == 1 ? bf16_to_f32(f32_to_bf16(x)) : x; }
+
+__device__ __forceinline__ void load_row32(const PostOp &q, int64_t grow, bool row_ok, int col, int N,
+                                           float (&x)[32]) {
+  if (row_ok && q.xvec && col + 32 <= N) {
+    if (q.x_dt == 1) {
+      const uint4 *src = reinterpret_cast<const uint4 *>(static_cast<const uint16_t *>(q.X) + grow * q.ldx + col);
+      uint4 w[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) w[k] = __ldcg(src + k);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t ww[4] = {w[k].x, w[k].y, w[k].z, w[k].w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          x[8 * k + 2 * i] = __uint_as_float(ww[i] << 16);
+          x[8 * k + 2 * i + 1] = __uint_as_float(ww[i] & 0xFFFF0000u);
+        }
+      }
+    } else {
+      const float4 *src = reinterpret_cast<const float4 *>(static_cast<const float *>(q.X) + grow * q.ldx + col);
+      float4 w[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) w[k] = __ldcg(src + k);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        x[4 * k] = w[k].x; x[4 * k + 1] = w[k].y; x[4 * k + 2] = w[k].z; x[4 * k + 3] = w[k].w;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+      x[i] = (row_ok && col + i < N) ? load_elem(q.X, q.x_dt, grow * q.ldx + col + i) : 0.f;
+  }
+}
+
+__device__ __forceinline__ void post_ops(const NodeParams &np, float (&v)[32], int64_t grow, bool row_ok, int col,
+                                         int N) {
+  int dt = np.o_dt;
+  for (int j = 0; j < np.n_post; ++j) {
+    const PostOp &q = np.post[j];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = round_dt(dt, v[i]);
+    if (q.X) {
+      float x[32];
+      load_row32(q, grow, row_ok, col, N, x);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) v[i] = activate(q.act, v[i] + x[i]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) v[i] = activate(q.act, v[i]);
+    }
+    dt = q.out_dt;
+  }
+}
+
 // Epilogue (workers): TMEM accumulator -> scale, bias, activation, cast ->
 // global.  Worker warp w reads TMEM lanes 32*(w%4).. and the columns of half
 // (w-4)/4 of the tile; each thread owns one output row.  With an output
 // tensor map, the two warps of a quadrant take alternate 128-byte column
 // chunks of their 32 rows and write each through a
 // 128-byte-swizzled shared staging block (one TMA store per chunk, clipped at
-// the buffer's edges); otherwise it stores directly.
+// the buffer's edges); otherwise it stores directly.  Fused elementwise
+// kernels (npg.n_post) run on the values before the cast; C is then the last
+// one's output (kPost; the executor is built with and without that code).
+template <bool kPost>
 __device__ __forceinline__ void gemm_epilogue(const ExecParams &p, const TileDesc &t, const NodeParams &npg,
                                               const SmemCtl *ctl, uint32_t tmem_acc, uint8_t *scratch) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -485,6 +549,10 @@ __device__ __forceinline__ void gemm_epilogue(const ExecParams &p, const TileDes
         add_parts(v, c + sub);
 #pragma unroll
         for (int i = 0; i < 32; ++i) v[i] = activate(act, fmaf(v[i], scale, ctl->bias[c + sub + i]));
+        if constexpr (kPost) {
+          const int row = m0 + trow_local;
+          post_ops(npg, v, (int64_t)bt * M + row, row < M, n0 + c + sub, N);
+        }
         // 16-byte chunk j of this row goes to position j ^ (row % 8) (128-byte swizzle)
         if (c_dt == 1) {
 #pragma unroll
@@ -531,6 +599,7 @@ __device__ __forceinline__ void gemm_epilogue(const ExecParams &p, const TileDes
     if (col >= N || !row_ok) continue;
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = activate(act, fmaf(v[i], scale, ctl->bias[c + i]));
+    if constexpr (kPost) post_ops(npg, v, grow, true, col, N);
     if (vec && col + 32 <= N) {
       if (c_dt == 1) {
         uint4 *dst = reinterpret_cast<uint4 *>(static_cast<uint16_t *>(Cp) + grow * ldc + col);

@@ -136,6 +136,9 @@ class Dag:
     def tiles(self):
         return abi.dag_tiles_get(self.h)
 
+    def fusion(self):
+        return abi.dag_fusion_get(self.h)
+
     def plan(self):
         return abi.dag_plan_get(self.h)
 

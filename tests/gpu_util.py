@@ -20,15 +20,26 @@ def node_tolerance(w, bid):
     return TOL[w.buffers[bid].dtype] if w.buffers[bid].dtype == BF16 else TOL[F32]
 
 
-def written_buffers(w):
-    return sorted({n.out for n in w.nodes})
+def written_buffers(w, fused=None):
+    """Buffers the DAG's kernels write.  With the library's fusion map
+    (kernel -> the GEMM whose epilogue computes it, or -1), the buffers a
+    fused kernel reads from its own chain are never written."""
+    outs = {n.out for n in w.nodes}
+    for e, h in enumerate(fused or []):
+        if h < 0:
+            continue
+        chain = [h] + [v for v, hh in enumerate(fused) if hh == h and v != e]
+        for u in chain:
+            if w.nodes[u].out in (w.nodes[e].a, w.nodes[e].b):
+                outs.discard(w.nodes[u].out)
+    return sorted(outs)
 
 
 def run_gpu(w, inputs, coarse=False, opts=None, resident=False, keep=False):
     d = Dag(w, opts, resident_inputs=resident)
     d.set_inputs(inputs)
     d.run(coarse=coarse)
-    outs = {b: d.output(b) for b in written_buffers(w)}
+    outs = {b: d.output(b) for b in written_buffers(w, d.fusion())}
     if keep:
         return d, outs
     d.close()
@@ -38,7 +49,7 @@ def run_gpu(w, inputs, coarse=False, opts=None, resident=False, keep=False):
 def compare(w, got, ref_store, bids=None):
     """{buffer: rel_err}; raises AssertionError above tolerance."""
     errs = {}
-    for b in bids or written_buffers(w):
+    for b in bids or sorted(got):
         dt = w.buffers[b].dtype
         g = storage_to_f64(got[b], dt)
         r = storage_to_f64(oracle.view(w, ref_store, b), dt)
@@ -53,7 +64,7 @@ def compare(w, got, ref_store, bids=None):
 def check_trace(w, d):
     recs = d.trace()
     trace_check.check(w, [(r.node, r.r0, r.r1, r.c0, r.c1) for r in recs], [r.split for r in recs],
-                      [r.start_ticket for r in recs], [r.end_ticket for r in recs])
+                      [r.start_ticket for r in recs], [r.end_ticket for r in recs], d.fusion())
     return recs
 
 

@@ -170,7 +170,7 @@ def test_queue_order_is_a_legal_schedule(name, make, n_sm):
         t, info = abi.dag_plan_host(n, e, b, opts, n_sm)
         assert info.n_tiles == len(t) > 0
         start = np.arange(len(t), dtype=np.uint32) * 2
-        trace_check.check(w, t[:, :5], t[:, 5] >> 16, start, start + 1)
+        trace_check.check(w, t[:, :5], t[:, 5] >> 16, start, start + 1, abi.dag_fusion_host(n, e, b, opts))
 
 
 def test_plan_algorithmic_totals():

@@ -25,7 +25,7 @@ def lib():
 
 
 def _outputs(d, w):
-    return {b: d.output(b) for b in written_buffers(w)}
+    return {b: d.output(b) for b in written_buffers(w, d.fusion())}
 
 
 def _preds(w):

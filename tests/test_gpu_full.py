@@ -10,7 +10,8 @@ from paper_2009_07482_gb300 import _binding as abi
 from paper_2009_07482_gb300.dag import Dag, options
 from synth import BF16, F32, storage_to_f64
 from synth.workloads import branchy_mlp, concat, encoder_block, fork_join, random_batch, random_layered
-from tests.gpu_util import bits_equal, check_trace, compare, node_tolerance, run_gpu
+from tests.gpu_util import bits_equal, check_trace, compare, node_tolerance, run_gpu, written_buffers
+from tests import trace_check
 from tests.row_sample import oracle_rows
 
 pytestmark = pytest.mark.gpu
@@ -54,7 +55,7 @@ def test_fork_join_full_size():
     d = Dag(w, options(trace=1), resident_inputs=True)
     d.set_inputs(ins)
     d.run()
-    compare(w, {b: d.output(b) for b in sorted({n.out for n in w.nodes})}, oracle.run(w, ins))
+    compare(w, {b: d.output(b) for b in written_buffers(w, d.fusion())}, oracle.run(w, ins))
     check_trace(w, d)
     d.close()
 
@@ -95,6 +96,7 @@ def test_batched_random_dags_full_size():
     d.run()
     d.run()   # a replay of the captured graph
     recs = d.trace()
+    fusion = d.fusion()
     rows = np.array([0, 31, 63])
     for k in (0, 1, 17, 100, 200, 255):
         w = ws[k]
@@ -103,8 +105,9 @@ def test_batched_random_dags_full_size():
         _check_rows(w, ins, got, rows, list(got))
         sub = [r for r in recs if noffs[k] <= r.node < noffs[k + 1]]
         tiles = np.array([(r.node - noffs[k], r.r0, r.r1, r.c0, r.c1) for r in sub], np.int32)
-        rc = oracle.check_trace(w, tiles, [r.start_ticket for r in sub], [r.end_ticket for r in sub])
-        assert rc[0] == 0, (k, rc)
+        fused = [h - noffs[k] if h >= 0 else -1 for h in fusion[noffs[k]:noffs[k + 1]]]
+        trace_check.check(w, tiles, [r.split for r in sub], [r.start_ticket for r in sub],
+                          [r.end_ticket for r in sub], fused)
     d.close()
 
 
@@ -120,7 +123,7 @@ def test_batch_of_small_dags_matches_oracle_and_graph_replay():
         d.set_inputs(ins)
         for _ in range(2):
             d.run()
-        got = {b: d.output(b) for b in sorted({n.out for n in w.nodes})}
+        got = {b: d.output(b) for b in written_buffers(w, d.fusion())}
         compare(w, got, ref)
         check_trace(w, d)
         outs[graph] = got
@@ -136,5 +139,5 @@ def test_autotuner_picks_a_measured_plan():
     assert info.tuned_us > 0 and info.tile_override in (0, 128, 256)
     d.set_inputs(ins)
     d.run()
-    compare(w, {b: d.output(b) for b in sorted({n.out for n in w.nodes})}, oracle.run(w, ins))
+    compare(w, {b: d.output(b) for b in written_buffers(w, d.fusion())}, oracle.run(w, ins))
     d.close()

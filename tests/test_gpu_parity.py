@@ -13,7 +13,7 @@ from paper_2009_07482_gb300 import _binding as abi
 from paper_2009_07482_gb300.dag import Dag, options
 from synth import BF16, F32
 from synth.workloads import Workload, branchy_mlp, encoder_block, fork_join, random_layered
-from tests.gpu_util import bits_equal, check_trace, compare, run_gpu
+from tests.gpu_util import bits_equal, check_trace, compare, run_gpu, written_buffers
 
 pytestmark = pytest.mark.gpu
 
@@ -31,7 +31,7 @@ def _roundtrip(w, opts=None, coarse_too=True):
     d = Dag(w, opts or options(trace=1))
     d.set_inputs(ins)
     d.run()
-    got = {b: d.output(b) for b in sorted({n.out for n in w.nodes})}
+    got = {b: d.output(b) for b in written_buffers(w, d.fusion())}
     errs = compare(w, got, ref)
     check_trace(w, d)
     if coarse_too:
@@ -290,7 +290,7 @@ def test_gemm_split_k(case):
     d = Dag(w, options(max_ctas=3), resident_inputs=True)
     d.set_inputs(ins)
     d.run()
-    outs = {b: d.output(b) for b in sorted({n.out for n in w.nodes})}
+    outs = {b: d.output(b) for b in written_buffers(w, d.fusion())}
     d.run()
     again = {b: d.output(b) for b in outs}
     d.run_cq(n_queues=2, components=abi.DAG_TC_PER_KERNEL)
