@@ -138,7 +138,11 @@ typedef struct {
                                  GEMM whose output they read, when that output has no other reader, is no
                                  view and no DAG input or output (up to 2 in a chain per GEMM; each step is
                                  rounded to its buffer's dtype exactly as if stored: bit-identical results) */
-  int32_t reserved[2];
+  int32_t keep_layout;        /* 0: a resident bf16/f32 input read only as the B operand of GEMMs with
+                                 trans_b = 0 (all with one shape) is kept transposed (N x K per batch) on
+                                 the device, made from its given layout at upload, so the tensor cores read
+                                 it K-major; 1: every buffer keeps the caller's layout */
+  int32_t reserved[1];
 } dag_options;
 
 /* Epilogue fusion (dag_options.fuse).  DAG_FUSE_NONE (default): every kernel
@@ -200,7 +204,8 @@ dag_status dag_set_input(dag_handle *h, int buf, const void *host_ptr);
 
 /* dag_set_output: host destination (rows x cols, dense) that every following
  * dag_submit fills after the kernel (device->host on a copy stream); NULL
- * cancels.  Same lifetime rule as dag_set_input. */
+ * cancels.  Same lifetime rule as dag_set_input.  DAG_EINVAL for a weight
+ * kept transposed on the device (dag_options.keep_layout). */
 dag_status dag_set_output(dag_handle *h, int buf, void *host_ptr);
 
 /*
@@ -278,11 +283,13 @@ dag_status dag_wait(dag_handle *h, uint64_t timeout_ns);
 dag_status dag_poll(dag_handle *h);
 
 /* dag_get_output: synchronous device->host copy of buffer `buf` (rows x cols,
- * dense) into host_ptr; call after dag_wait. */
+ * dense, the caller's layout even for a weight kept transposed on the
+ * device) into host_ptr; call after dag_wait. */
 dag_status dag_get_output(dag_handle *h, int buf, void *host_ptr);
 
 /* dag_device_ptr: device address of buffer `buf` (borrowed, valid until
- * dag_destroy) and its row pitch in elements; NULL on a bad id. */
+ * dag_destroy) and its row pitch in elements; NULL on a bad id and for a
+ * weight kept transposed on the device (dag_options.keep_layout). */
 const void *dag_device_ptr(dag_handle *h, int buf, int64_t *ld_elems);
 
 /* dag_destroy: wait for outstanding work (bounded), free everything. */

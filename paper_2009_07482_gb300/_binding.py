@@ -49,7 +49,7 @@ class dag_options(C.Structure):
     _fields_ = [("timeout_ns", u64), ("trace", i32), ("max_ctas", i32), ("scheduler", i32),
                 ("tile_override", i32), ("node_cost_us", C.POINTER(f32)), ("debug_never_ready", i32),
                 ("use_graph", i32), ("autotune", i32), ("f32_gemm", i32), ("split_k", i32), ("fuse", i32),
-                ("reserved", i32 * 2)]
+                ("keep_layout", i32), ("reserved", i32 * 1)]
 
 
 class dag_cq_options(C.Structure):

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libdagexec.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["exec_kernel.cu", "dagexec_host.cpp", "noalloc.cu", "costmodel.cu", "server.cpp"]
+SOURCES = ["exec_kernel.cu", "dagexec_host.cpp", "noalloc.cu", "costmodel.cu", "server.cpp", "layout.cu"]
 
 
 def _nvcc() -> str:

@@ -165,6 +165,10 @@ int exec_smem_bytes();
 cudaError_t exec_prepare();  // sets the kernel's shared-memory attribute (once per process)
 cudaError_t launch_persistent(const ExecParams &p, int grid, cudaStream_t s);
 cudaError_t launch_coarse(const ExecParams &p, int tile_begin, int n, cudaStream_t s);
+// dst (batch blocks of N x K, row pitch ldd) = per-block transpose of src
+// (batch blocks of K x N, row pitch lds); elem_bytes 2 or 4 (layout.cu)
+cudaError_t launch_transpose(const void *src, int64_t lds, void *dst, int64_t ldd, int batch, int K, int N,
+                             int elem_bytes, cudaStream_t st);
 int max_coresident_ctas_per_sm();
 
 // Plan a DAG over caller-owned device buffers and serialise every device-side

@@ -363,6 +363,9 @@ struct Plan {
   std::vector<int> cfg;                 // per node tile config
   std::vector<char> tf32;               // per node: f32 GEMM on the tensor cores (3 x TF32)
   std::vector<int> nsplit;              // per node: split-K factor S (0 = none)
+  std::vector<char> store_t;            // per buffer: a weight kept transposed on the device (layout.cu)
+  std::vector<int> t_batch, t_K, t_N;   // its per-batch shape as given (K x N)
+  bool allow_layout = true;             // not for caller-owned buffers (the no-alloc entry point)
   std::vector<int> absorbed_by;         // per node: the GEMM whose epilogue computes it, or -1
   std::vector<std::vector<int>> post;   // per GEMM: elementwise kernels fused into its epilogue, in order
   bool allow_split = true;              // split K needs scratch memory (not in the no-alloc entry point)
@@ -476,6 +479,47 @@ static void choose_configs(Plan &P) {
     } else {
       P.cfg[v] -= 100;
     }
+  }
+}
+
+// Weights kept K-major on the device: a resident bf16/f32 input buffer that
+// every reader takes as the B operand of a GEMM with trans_b = 0, all with
+// one (batch, K, N), with no views into it.  The GEMMs then run as trans_b =
+// 1 over the transposed copy (see layout.cu).
+static void choose_layouts(Plan &P) {
+  Graph &g = P.g;
+  P.store_t.assign(g.nb, 0);
+  P.t_batch.assign(g.nb, 0);
+  P.t_K.assign(g.nb, 0);
+  P.t_N.assign(g.nb, 0);
+  if (!P.allow_layout || P.opt.keep_layout) return;
+  std::vector<char> ok(g.nb, 1);
+  for (int b = 0; b < g.nb; ++b)
+    if (g.root[b] != b) ok[g.root[b]] = 0;  // read through a view
+  std::vector<int> readers(g.nb, 0);
+  for (int v = 0; v < g.nn; ++v) {
+    const dag_node_desc &n = g.nodes[v];
+    int in[3];
+    const int k = g.inputs(v, in);
+    for (int q = 0; q < k; ++q) {
+      const int r = g.root[in[q]];
+      readers[r]++;
+      if (n.op != DAG_OP_GEMM || q != 1 || n.trans_b || in[0] == in[1] || (k > 2 && in[2] == in[1])) {
+        ok[r] = 0;
+        continue;
+      }
+      if (readers[r] == 1) {
+        P.t_batch[r] = n.batch; P.t_K[r] = g.K[v]; P.t_N[r] = g.N[v];
+      } else if (P.t_batch[r] != n.batch || P.t_K[r] != g.K[v] || P.t_N[r] != g.N[v]) {
+        ok[r] = 0;
+      }
+    }
+  }
+  for (int b = 0; b < g.nb; ++b) {
+    const dag_buffer_desc &d = g.bufs[b];
+    const uint32_t want = DAG_BUF_INPUT | DAG_BUF_RESIDENT;
+    P.store_t[b] = ok[b] && readers[b] > 0 && g.root[b] == b && (d.flags & want) == want &&
+                   (d.dtype == DAG_BF16 || d.dtype == DAG_F32);
   }
 }
 
@@ -909,6 +953,7 @@ static void roofline(Plan &P) {
 
 static void plan_tiles(Plan &P) {
   choose_configs(P);
+  choose_layouts(P);
   choose_fusion(P);
   choose_split(P);
   make_tiles(P);
@@ -963,6 +1008,9 @@ struct dag_handle {
   void *arena = nullptr;      // buffers
   void *meta = nullptr;       // plan arrays
   float *split_scratch = nullptr;  // split K partial sums
+  void *staging = nullptr;         // upload area of weights kept transposed
+  cudaEvent_t ev_staging = nullptr;
+  bool staging_used = false;
   std::vector<char *> dptr;   // per buffer (view-adjusted)
   std::vector<int64_t> ld;    // per buffer row pitch (elements)
   ExecParams xp{};            // persistent-mode parameters
@@ -1004,6 +1052,8 @@ static void free_handle(dag_handle *h) {
   if (h->arena) cudaFree(h->arena);
   if (h->meta) cudaFree(h->meta);
   if (h->split_scratch) cudaFree(h->split_scratch);
+  if (h->staging) cudaFree(h->staging);
+  if (h->ev_staging) cudaEventDestroy(h->ev_staging);
   for (auto &s : h->up)
     if (s) cudaStreamDestroy(s);
   if (h->down) cudaStreamDestroy(h->down);
@@ -1062,7 +1112,7 @@ static dag_status gemm_maps(const Plan &P, int v, NodeParams &q, std::vector<CUt
   CUtensorMap ma, mb;
   dag_status s;
   if ((s = encode_map(&ma, q.A, K, M, B, q.lda * es, (uint64_t)M * q.lda * es, kb, kBM, dt))) return s;
-  if (n.trans_b) s = encode_map(&mb, q.B, K, N, B, q.ldb * es, (uint64_t)N * q.ldb * es, kb, bn, dt);
+  if (q.trans_b) s = encode_map(&mb, q.B, K, N, B, q.ldb * es, (uint64_t)N * q.ldb * es, kb, bn, dt);
   else s = encode_map(&mb, q.B, N, K, B, q.ldb * es, (uint64_t)K * q.ldb * es, 128 / es, kb, dt);
   if (s) return s;
   q.tmap_a = (int)maps.size(); maps.push_back(ma);
@@ -1094,7 +1144,9 @@ static dag_status fill_params(const Plan &P, int v, char *const *dptr, const int
   q.c_dt = g.bufs[out].dtype;
   q.o_dt = g.bufs[n.out].dtype;
   q.M = g.M[v]; q.N = g.N[v]; q.K = g.K[v]; q.batch = n.op == DAG_OP_GEMM ? n.batch : 1;
-  q.trans_b = n.trans_b; q.act = n.act; q.scale = n.scale;
+  // a weight kept transposed is read K-major
+  q.trans_b = n.trans_b || (n.op == DAG_OP_GEMM && P.store_t[g.root[n.b]]);
+  q.act = n.act; q.scale = n.scale;
   q.tmap_a = q.tmap_b = q.tmap_c = -1;
   // 16-byte vector paths: every operand starts on a 16-byte boundary (row
   // pitches are multiples of 16 bytes)
@@ -1149,11 +1201,21 @@ static dag_status create_impl(const dag_node_desc *nodes, int n_nodes, const dag
   h->ld.assign(g.nb, 0);
   std::vector<size_t> off(g.nb, 0);
   size_t total = 0;
+  size_t stage_bytes = 0;
   for (int b = 0; b < g.nb; ++b) {
     if (g.bufs[b].view_of >= 0) continue;
-    h->ld[b] = round_up(g.bufs[b].cols, 16);
+    const int es = esize(g.bufs[b].dtype);
+    // a weight kept transposed: batch blocks of N x K
+    const int64_t rows = P.store_t[b] ? (int64_t)P.t_batch[b] * P.t_N[b] : g.bufs[b].rows;
+    h->ld[b] = round_up(P.store_t[b] ? P.t_K[b] : g.bufs[b].cols, 16);
     off[b] = total;
-    total = align_up(total + (size_t)g.bufs[b].rows * h->ld[b] * esize(g.bufs[b].dtype), 1024);
+    total = align_up(total + (size_t)rows * h->ld[b] * es, 1024);
+    if (P.store_t[b]) stage_bytes = std::max(stage_bytes, (size_t)g.bufs[b].rows * g.bufs[b].cols * es);
+  }
+  if (stage_bytes && (cudaMalloc(&h->staging, stage_bytes) != cudaSuccess ||
+                      cudaEventCreateWithFlags(&h->ev_staging, cudaEventDisableTiming) != cudaSuccess)) {
+    free_handle(h);
+    return fail(DAG_ENOMEM, "weight staging (%zu bytes)", stage_bytes);
   }
   if (total && cudaMalloc(&h->arena, total) != cudaSuccess) { free_handle(h); return fail(DAG_ENOMEM, "device buffers (%zu bytes)", total); }
   if (total) cudaMemset(h->arena, 0, total);
@@ -1350,6 +1412,8 @@ extern "C" dag_status dag_set_output(dag_handle *h, int buf, void *host_ptr) {
   dag_status s = check_handle(h);
   if (s) return s;
   if (buf < 0 || buf >= h->P.g.nb) return fail(DAG_EINVAL, "bad buffer %d", buf);
+  if (h->P.store_t[h->P.g.root[buf]])
+    return fail(DAG_EINVAL, "buffer %d is a weight kept transposed on the device: read it with dag_get_output", buf);
   if (h->in_flight) return fail(DAG_EBUSY, "a submit is in flight");
   h->host_out[buf] = host_ptr;
   return DAG_OK;
@@ -1357,6 +1421,18 @@ extern "C" dag_status dag_set_output(dag_handle *h, int buf, void *host_ptr) {
 
 static cudaError_t copy_h2d(dag_handle *h, int b, cudaStream_t st) {
   const dag_buffer_desc &d = h->P.g.bufs[b];
+  const Plan &P = h->P;
+  if (P.store_t[b]) {  // through the staging area (one upload at a time, in any stream), then transposed
+    cudaError_t e = cudaSuccess;
+    if (h->staging_used) e = cudaStreamWaitEvent(st, h->ev_staging, 0);
+    if (!e) e = cudaMemcpyAsync(h->staging, h->host_in[b], (size_t)d.rows * d.cols * esize(d.dtype),
+                                cudaMemcpyHostToDevice, st);
+    if (!e) e = launch_transpose(h->staging, d.cols, h->dptr[b], h->ld[b], P.t_batch[b], P.t_K[b], P.t_N[b],
+                                 esize(d.dtype), st);
+    if (!e) e = cudaEventRecord(h->ev_staging, st);
+    h->staging_used = true;
+    return e;
+  }
   const size_t w = (size_t)d.cols * esize(d.dtype);
   return cudaMemcpy2DAsync(h->dptr[b], (size_t)h->ld[b] * esize(d.dtype), h->host_in[b], w, w, d.rows,
                            cudaMemcpyHostToDevice, st);
@@ -1545,13 +1621,27 @@ extern "C" dag_status dag_get_output(dag_handle *h, int buf, void *host_ptr) {
   if (buf < 0 || buf >= h->P.g.nb || !host_ptr) return fail(DAG_EINVAL, "bad buffer or pointer");
   if (h->in_flight) return fail(DAG_EBUSY, "call dag_wait first");
   const dag_buffer_desc &d = h->P.g.bufs[buf];
-  const size_t w = (size_t)d.cols * esize(d.dtype);
-  CUDA_TRY(cudaMemcpy2D(host_ptr, w, h->dptr[buf], (size_t)h->ld[buf] * esize(d.dtype), w, d.rows, cudaMemcpyDeviceToHost));
+  const int es = esize(d.dtype);
+  const size_t w = (size_t)d.cols * es;
+  const Plan &P = h->P;
+  if (P.store_t[buf]) {  // back to the caller's layout on the host
+    const int64_t B = P.t_batch[buf], K = P.t_K[buf], N = P.t_N[buf];
+    std::vector<char> t((size_t)B * N * K * es);
+    CUDA_TRY(cudaMemcpy2D(t.data(), (size_t)K * es, h->dptr[buf], (size_t)h->ld[buf] * es, (size_t)K * es, B * N,
+                          cudaMemcpyDeviceToHost));
+    char *out = static_cast<char *>(host_ptr);
+    for (int64_t b = 0; b < B; ++b)
+      for (int64_t n = 0; n < N; ++n)
+        for (int64_t k = 0; k < K; ++k)
+          memcpy(out + ((b * K + k) * N + n) * es, t.data() + ((b * N + n) * K + k) * es, es);
+    return DAG_OK;
+  }
+  CUDA_TRY(cudaMemcpy2D(host_ptr, w, h->dptr[buf], (size_t)h->ld[buf] * es, w, d.rows, cudaMemcpyDeviceToHost));
   return DAG_OK;
 }
 
 extern "C" const void *dag_device_ptr(dag_handle *h, int buf, int64_t *ld_elems) {
-  if (!h || buf < 0 || buf >= h->P.g.nb) return nullptr;
+  if (!h || buf < 0 || buf >= h->P.g.nb || h->P.store_t[h->P.g.root[buf]]) return nullptr;
   if (ld_elems) *ld_elems = h->ld[buf];
   return h->dptr[buf];
 }
@@ -1693,6 +1783,7 @@ dag_status dagx::plan_into_region(const dag_node_desc *nodes, int n_nodes, const
   P.opt.trace = 0;
   P.opt.debug_never_ready = 0;
   P.allow_split = false;  // split K needs scratch memory
+  P.allow_layout = false; // caller-owned buffers keep the caller's layout
   // every input is already in the caller's device memory: no upload flags
   std::vector<dag_buffer_desc> bufs(buffers, buffers + std::max(0, n_buffers));
   for (auto &b : bufs)
