@@ -666,7 +666,8 @@ def main():
     # the opt-in epilogue-fusion modes (the measured line runs without fusion)
     unfused = None
     for name, mode in (("activations", abi.DAG_FUSE_ACT), ("activations_and_adds", abi.DAG_FUSE_ALL)):
-        n_f = sum(h >= 0 for h in abi.dag_fusion_host(*describe(w, resident_inputs=True), options(fuse=mode)))
+        fo = options(fuse=mode, f32_gemm=abi.DAG_F32_GEMM_SIMT if args.f32_simt else 0)
+        n_f = sum(h >= 0 for h in abi.dag_fusion_host(*describe(w, resident_inputs=True), fo))
         if not n_f:
             continue
         u = make_dag(False, fuse=mode)
