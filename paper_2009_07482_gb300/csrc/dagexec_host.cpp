@@ -652,12 +652,20 @@ static void make_tiles(Plan &P) {
               if (S) P.tiles.back().split = (s << 8) | S;
             }
     } else if (n.op == DAG_OP_SOFTMAX) {
-      // memory-bound and latency-bound per SM (a warp keeps two rows in
-      // flight): 16..64 rows, split further while the level has fewer than
-      // its share of two tiles per SM
-      const double share = 2.0 * P.n_sm * ((double)R * C) / std::max(1.0, level_elems[dep[v]]);
-      int rows = C <= 1024 ? 64 : 16;
-      while (rows > 16 && (double)((R + rows - 1) / rows) < share) rows /= 2;
+      // memory-bound and latency-bound per SM (a warp keeps eight rows of
+      // up to 256 elements in flight).  A softmax that other kernels read:
+      // 32..64 rows (16..64 for longer rows), split further while the level
+      // has fewer than its share of two tiles per SM, so that its consumers
+      // start on early rows.  A softmax nothing reads: one wave of tiles of
+      // up to 256 rows, which stream longer per dependency hand-off.
+      const bool sink = g.succ[v].empty();
+      const double share = (sink ? 1.0 : 2.0) * P.n_sm * ((double)R * C) / std::max(1.0, level_elems[dep[v]]);
+      const int lo = C <= 256 ? 32 : 16;
+      int rows = sink && C <= 256 ? 256 : C <= 1024 ? 64 : 16;
+      if (sink)
+        while (rows > lo && (double)((R + rows / 2 - 1) / (rows / 2)) <= share) rows /= 2;
+      else
+        while (rows > lo && (double)((R + rows - 1) / rows) < share) rows /= 2;
       for (int r = 0; r < R; r += rows) push(T_SOFTMAX, r, std::min(r + rows, R), 0, C, 0);
     } else {
       // at most 64K and at least 4K elements per tile, split further while
