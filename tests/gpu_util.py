@@ -22,16 +22,19 @@ def node_tolerance(w, bid):
 
 def written_buffers(w, fused=None):
     """Buffers the DAG's kernels write.  With the library's fusion map
-    (kernel -> the GEMM whose epilogue computes it, or -1), the buffers a
-    fused kernel reads from its own chain are never written."""
+    (kernel -> the kernel whose tiles compute it, or -1), a buffer that one
+    kernel of a fused group writes and another of the group reads is never
+    written."""
     outs = {n.out for n in w.nodes}
-    for e, h in enumerate(fused or []):
-        if h < 0:
-            continue
-        chain = [h] + [v for v, hh in enumerate(fused) if hh == h and v != e]
-        for u in chain:
-            if w.nodes[u].out in (w.nodes[e].a, w.nodes[e].b):
-                outs.discard(w.nodes[u].out)
+    groups = {}
+    for v, h in enumerate(fused or []):
+        if h >= 0:
+            groups.setdefault(h, {h}).add(v)
+    for g in groups.values():
+        for x in g:
+            for y in g:
+                if x != y and w.nodes[y].out in (w.nodes[x].a, w.nodes[x].b):
+                    outs.discard(w.nodes[y].out)
     return sorted(outs)
 
 

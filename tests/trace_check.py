@@ -8,56 +8,55 @@ its reads are checked against their producers and its consumers must start
 after it.  Then every partial must
 have ended before its region's finishing partial started.
 
-A tile of a GEMM with fused elementwise kernels (the library's fusion map:
-kernel -> the GEMM that computes it, or -1) stands for one tile of each kernel
-of its chain on the same region.  Tickets are scaled by 8 and the chain's
-tiles placed in chain order between the tile's start and end tickets: the
-GEMM's right after the start, each fused kernel's after the previous one's,
-the last one ending at the tile's end.  The start ticket of such a tile is
-drawn after the waits of its epilogue, so each fused kernel's other operand
-must have been released before it."""
+A tile of a fused group (the library's fusion map: kernel -> the kernel whose
+tiles compute it, or -1) -- a GEMM with elementwise kernels in its epilogue,
+or an add computing the adds that feed it -- stands for one tile of each
+kernel of the group on the same region.  Tickets are scaled by 8 and the
+group's tiles placed in dependency order between the tile's start and end
+tickets, the last one ending at the tile's end.  The start ticket of such a
+tile is drawn after all its waits, so every operand of the group must have
+been released before it."""
 import numpy as np
 
 import oracle
 
 
-def _chains(w, fused):
-    """head GEMM -> its fused kernels in chain order (each reads the previous output)."""
+def _groups(w, fused):
+    """head -> the kernels its tiles compute (itself included) in dependency order."""
     members = {}
     for v, h in enumerate(fused or []):
         if h >= 0:
             members.setdefault(h, []).append(v)
-    chains = {}
+    groups = {}
     for h, ms in members.items():
-        prev, order, left = w.nodes[h].out, [], list(ms)
+        left, order = [h] + ms, []
         while left:
-            nxt = [v for v in left if prev in (w.nodes[v].a, w.nodes[v].b)]
-            assert len(nxt) == 1, f"fused kernels of {h} do not form a chain"
-            order.append(nxt[0])
-            left.remove(nxt[0])
-            prev = w.nodes[nxt[0]].out
-        chains[h] = order
-    return chains
+            outs = {w.nodes[u].out for u in left}
+            ready = [v for v in left if not ({w.nodes[v].a, w.nodes[v].b} & outs - {w.nodes[v].out})]
+            assert ready, f"fused kernels of {h} form a cycle"
+            order.append(ready[0])
+            left.remove(ready[0])
+        groups[h] = order
+    return groups
 
 
 def expand_fused(w, tiles5, split, start, end, fused):
-    chains = _chains(w, fused)
+    groups = _groups(w, fused)
     T, S, st, en = [], [], [], []
     for i, t in enumerate(np.asarray(tiles5, np.int64)):
         s8, e8 = 8 * int(start[i]), 8 * int(end[i])
         node = int(t[0])
         sp = int(split[i])
         partial = (sp & 0xFF) and (sp >> 8) < (sp & 0xFF) - 1
-        chain = chains.get(node, [])
-        if not chain or partial:
+        group = groups.get(node)
+        if not group or partial:  # a split partial computes the GEMM alone
             T.append(t); S.append(sp); st.append(s8); en.append(e8)
             continue
-        T.append(t); S.append(sp); st.append(s8); en.append(s8 + 1)
-        for j, m in enumerate(chain):
+        for j, m in enumerate(group):
             T.append(np.array([m, t[1], t[2], t[3], t[4]]))
-            S.append(0)
-            st.append(s8 + 2 * (j + 1))
-            en.append(s8 + 2 * (j + 1) + 1 if j + 1 < len(chain) else e8)
+            S.append(sp if m == node else 0)
+            st.append(s8 + 2 * j)
+            en.append(s8 + 2 * j + 1 if j + 1 < len(group) else e8)
     return (np.array(T, np.int32).reshape(-1, 5), np.array(S, np.int32), np.array(st, np.uint64),
             np.array(en, np.uint64))
 
