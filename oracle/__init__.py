@@ -61,33 +61,45 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-D_DEFAULT_SOURCE", _SRC, "-o", tmp, "-lm"])
+        compile_source(_SRC, tmp)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
+
+
+def compile_source(src: str, out: str) -> None:
+    """gcc, plain C99, no fused multiply-add contraction (x86 and Arm agree)."""
+    subprocess.check_call(["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                           "-D_DEFAULT_SOURCE", src, "-o", out, "-lm"])
+
+
+def load(path: str):
+    """Open a compiled oracle library and declare its entry points.  ``lib()``
+    uses the build of ``oracle.c``; the mutation tests load deliberately broken
+    copies through here."""
+    L = C.CDLL(path)
+    P = C.POINTER
+    L.or_f64_to_bf16.argtypes = [C.c_double]
+    L.or_f64_to_bf16.restype = C.c_uint16
+    L.or_validate.argtypes = [P(Buf), C.c_int, P(Nd), C.c_int]
+    L.or_topo_order.argtypes = [P(Buf), C.c_int, P(Nd), C.c_int, P(C.c_int32)]
+    L.or_is_topological.argtypes = [P(Buf), P(Nd), C.c_int, P(C.c_int32)]
+    L.or_run.argtypes = [P(Buf), C.c_int, P(Nd), C.c_int, P(C.c_void_p), P(C.c_int32)]
+    L.or_run_node.argtypes = [P(Buf), C.c_int, P(Nd), C.c_int, P(C.c_void_p), C.c_int,
+                              C.c_int64, C.c_int64]
+    L.or_run_tiles.argtypes = [P(Buf), C.c_int, P(Nd), C.c_int, P(C.c_void_p), P(Tile), C.c_int,
+                               P(C.c_int32)]
+    L.or_make_tiles.argtypes = [P(Buf), P(Nd), C.c_int, C.c_int, C.c_int, P(Tile), C.c_int]
+    L.or_tile_deps.argtypes = [P(Buf), P(Nd), P(Tile), C.c_int, P(C.c_int32), C.c_int]
+    L.or_check_trace.argtypes = [P(Buf), C.c_int, P(Nd), C.c_int, P(Tile), C.c_int,
+                                 P(C.c_uint32), P(C.c_uint32), P(C.c_int32), P(C.c_int32)]
+    return L
 
 
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = C.CDLL(build())
-            P = C.POINTER
-            L.or_f64_to_bf16.argtypes = [C.c_double]
-            L.or_f64_to_bf16.restype = C.c_uint16
-            L.or_validate.argtypes = [P(Buf), C.c_int, P(Nd), C.c_int]
-            L.or_topo_order.argtypes = [P(Buf), C.c_int, P(Nd), C.c_int, P(C.c_int32)]
-            L.or_is_topological.argtypes = [P(Buf), P(Nd), C.c_int, P(C.c_int32)]
-            L.or_run.argtypes = [P(Buf), C.c_int, P(Nd), C.c_int, P(C.c_void_p), P(C.c_int32)]
-            L.or_run_node.argtypes = [P(Buf), C.c_int, P(Nd), C.c_int, P(C.c_void_p), C.c_int,
-                                      C.c_int64, C.c_int64]
-            L.or_run_tiles.argtypes = [P(Buf), C.c_int, P(Nd), C.c_int, P(C.c_void_p), P(Tile), C.c_int,
-                                       P(C.c_int32)]
-            L.or_make_tiles.argtypes = [P(Buf), P(Nd), C.c_int, C.c_int, C.c_int, P(Tile), C.c_int]
-            L.or_tile_deps.argtypes = [P(Buf), P(Nd), P(Tile), C.c_int, P(C.c_int32), C.c_int]
-            L.or_check_trace.argtypes = [P(Buf), C.c_int, P(Nd), C.c_int, P(Tile), C.c_int,
-                                         P(C.c_uint32), P(C.c_uint32), P(C.c_int32), P(C.c_int32)]
-            _lib = L
+            _lib = load(build())
     return _lib
 
 

@@ -252,6 +252,19 @@ def test_validation_errors():
     p = w5.buf(4, 8, F32)
     w5.buf(4, 4, BF16, view_of=p, col_offset=4)
     assert oracle.validate(w5) == 4
+    for b_shape in [(4, 5), (5, 4)]:                  # an add's second operand of another shape
+        w6 = Workload("add_shape")
+        a = w6.buf(4, 4, F32, "input", ("uniform", 1))
+        b = w6.buf(*b_shape, F32, "input", ("uniform", 2))
+        w6.node("add", a, w6.buf(4, 4), b=b)
+        assert oracle.validate(w6) == 3, b_shape
+    for bias_shape in [(1, 3), (2, 4)]:               # a bias that is not one row of N
+        w7 = Workload("bias_shape")
+        a = w7.buf(4, 4, F32, "input", ("uniform", 1))
+        b = w7.buf(4, 4, F32, "input", ("uniform", 2))
+        bias = w7.buf(*bias_shape, F32, "input", ("uniform", 3))
+        w7.node("gemm", a, w7.buf(4, 4), b=b, bias=bias)
+        assert oracle.validate(w7) == 3, bias_shape
 
 
 # --------------------------------------------------------------------------
@@ -321,6 +334,23 @@ def test_every_topological_order_gives_identical_bits(make):
             assert np.array_equal(st[k].view(np.uint8), ref[k].view(np.uint8))
 
 
+def test_bias_produced_by_a_later_kernel_is_waited_for():
+    # kernel 0 reads as its bias the output of kernel 1 (an add): the order must
+    # be [1, 0], and the value is A.B + (x + y), exact in small integers
+    A = np.array([[1, 2], [3, -1]], float)
+    B = np.array([[2, 0, 1], [-1, 1, 3]], float)
+    x = np.array([[1, -2, 4]], float)
+    y = np.array([[3, 5, -1]], float)
+    w, ids = from_arrays("late_bias", {"A": (A, F32), "B": (B, F32), "x": (x, F32), "y": (y, F32)})
+    bias = w.buf(1, 3)
+    c = w.buf(2, 3, F32, "output")
+    w.node("gemm", ids["A"], c, b=ids["B"], bias=bias)
+    w.node("add", ids["x"], bias, b=ids["y"])
+    assert oracle.topo_order(w) == [1, 0]
+    st = oracle.run(w, w.make_inputs())
+    assert np.array_equal(st[c], (A @ B + x + y).astype(np.float32))
+
+
 def test_kahn_order_smallest_id_first():
     w = fork_join(8)
     assert oracle.topo_order(w) == [0, 1, 2, 3]
@@ -340,9 +370,42 @@ def _tiny_dags():
     w.node("softmax", h, s)
     w.node("unary", s, y, act="gelu")
     yield w, 4, 6
+    # a GEMM (kernel 0) whose B operand (8 x 8, two row blocks) and bias are
+    # written tile by tile by later kernels
+    w, ids = from_arrays("produced_operands", {"x": (synth.uniform(5, (4, 8)), F32),
+                                               "Ws": (synth.uniform(6, (8, 8)), F32),
+                                               "p": (synth.uniform(7, (1, 8)), F32),
+                                               "q": (synth.uniform(8, (1, 8)), F32)})
+    Wb = w.buf(8, 8)
+    bias = w.buf(1, 8)
+    y = w.buf(4, 8, F32, "output")
+    w.node("gemm", ids["x"], y, b=Wb, bias=bias)
+    w.node("unary", ids["Ws"], Wb, act="relu")
+    w.node("add", ids["p"], bias, b=ids["q"])
+    yield w, 4, 4
 
 
-@pytest.mark.parametrize("case", list(range(2)))
+def _random_linear_extensions(n, edges, count, seed):
+    """`count` linear extensions drawn by picking uniformly among the ready
+    tiles at every step (seeded), to reach orders far from the lexicographic
+    ones that _linear_extensions lists first."""
+    rng = np.random.default_rng(seed)
+    preds = {v: set() for v in range(n)}
+    for u, v in edges:
+        preds[v].add(u)
+    out = []
+    for _ in range(count):
+        placed, order = set(), []
+        while len(order) < n:
+            ready = [v for v in range(n) if v not in placed and preds[v] <= placed]
+            v = ready[int(rng.integers(len(ready)))]
+            placed.add(v)
+            order.append(v)
+        out.append(order)
+    return out
+
+
+@pytest.mark.parametrize("case", list(range(3)))
 def test_all_tile_orders_match_untiled(case):
     w, bm, bn = list(_tiny_dags())[case]
     ins = w.make_inputs()
@@ -352,6 +415,7 @@ def test_all_tile_orders_match_untiled(case):
     deps = oracle.tile_deps(w, tiles)
     orders = _linear_extensions(len(tiles), deps, limit=3000)
     assert len(orders) > 10
+    orders += _random_linear_extensions(len(tiles), deps, 300, seed=case)
     for o in orders:
         st = oracle.run_tiles(w, ins, tiles, o)
         for k in ref:
@@ -378,6 +442,29 @@ def test_all_tile_orders_match_untiled(case):
     assert rc == 3 and (bu, bv) in deps
 
 
+def test_softmax_tiles_split_by_columns():
+    # A softmax tile may cover part of a row: its statistics still span the
+    # whole row, and it depends on every producer tile of its rows.  Producer
+    # (GELU) and softmax are both tiled 4 x 4 over 8 x 8, so a softmax tile
+    # reads two producer tiles.
+    w, ids = from_arrays("split_softmax", {"x": (synth.uniform(9, (8, 8)) * 4, F32)})
+    h = w.buf(8, 8)
+    y = w.buf(8, 8, F32, "output")
+    w.node("unary", ids["x"], h, act="gelu")
+    w.node("softmax", h, y, scale=0.5)
+    ins = w.make_inputs()
+    ref = oracle.run(w, ins)
+    tiles = np.array([(k, r, r + 4, c, c + 4) for k in range(2) for r in (0, 4) for c in (0, 4)], np.int32)
+    deps = set(oracle.tile_deps(w, tiles))
+    for i, (k, r0, _, c0, _) in enumerate(tiles):
+        if k == 1:
+            assert {u for u, v in deps if v == i} == {j for j, t in enumerate(tiles) if t[0] == 0 and t[1] == r0}
+    orders = _linear_extensions(len(tiles), deps, limit=500) + _random_linear_extensions(len(tiles), deps, 200, 7)
+    for o in orders:
+        st = oracle.run_tiles(w, ins, tiles, o)
+        assert np.array_equal(st[y].view(np.uint8), ref[y].view(np.uint8))
+
+
 def test_trace_checker_coverage_and_ticket_errors():
     w = fork_join(8)
     tiles = oracle.make_tiles(w, 4, 4)
@@ -387,10 +474,20 @@ def test_trace_checker_coverage_and_ticket_errors():
     assert oracle.check_trace(w, tiles, start, end)[0] == 0
     assert oracle.check_trace(w, tiles[:-1], start[:-1], end[:-1])[0] == 1      # a hole
     dup = np.vstack([tiles, tiles[:1]])
-    assert oracle.check_trace(w, dup, np.append(start, 2 * n), np.append(end, 2 * n + 1))[0] == 1
+    rc, bu, _ = oracle.check_trace(w, dup, np.append(start, 2 * n), np.append(end, 2 * n + 1))
+    assert (rc, bu) == (1, n)                                                  # the second cover is named
     e2 = end.copy()
     e2[3] = start[3]
     assert oracle.check_trace(w, tiles, start, e2)[0] == 2
+    # tickets come from one counter, so end(u) == start(v) never happens in a
+    # legal run: the checker demands end(u) < start(v) strictly
+    deps = oracle.tile_deps(w, tiles)
+    v = deps[0][1]
+    u = max((a for a, b in deps if b == v), key=lambda a: end[a])          # v's last predecessor
+    s2 = start.copy()
+    s2[v] = end[u]
+    assert s2[v] < end[v]
+    assert oracle.check_trace(w, tiles, s2, end)[:3] == (3, u, v)
 
 
 def test_column_slice_views_depend_only_on_their_columns():
