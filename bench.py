@@ -51,7 +51,52 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="batched: skip the cost-model comparison")
     ap.add_argument("--profile", action="store_true", help="few steps, no side measurements (for ncu)")
     ap.add_argument("--f32-simt", action="store_true", help="f32 GEMMs on the SM cores (FFMA) instead of 3 x TF32")
+    ap.add_argument("--timeline", action="store_true",
+                    help="diagnostic: per-kernel phases of traced launches (claim, dependencies, K loop, epilogue, "
+                         "release) instead of the measured line")
     return ap.parse_args()
+
+
+# phases of one tile, in the order the executor stamps them (dag_trace_stamps)
+STAMPS = ["claim", "ready", "loaded", "mma0", "mma1", "work", "acc", "body", "sync", "end"]
+
+
+def run_timeline(args, w, d, abi, stream, flush, reps=8):
+    """Per-kernel timeline of `reps` traced launches of the handle `d`
+    (created with trace = 1): each kernel's window in the launch (first claim,
+    first dependency release, last release; medians over launches, in us from
+    the launch's first claim) and the median time of each phase of its tiles
+    (between consecutive stamps the tile kind records)."""
+    import numpy as np
+    windows, phases, spans = {}, {}, []
+    for _ in range(reps):
+        flush.zero_()
+        d.submit(stream.cuda_stream)
+        abi.check(d.wait(), "wait")
+        recs = d.trace()
+        st = abi.dag_trace_stamps(d.h).astype(np.int64)
+        node = np.array([r.node for r in recs])
+        t0 = st[:, 0].min()
+        spans.append((st[:, 9].max() - t0) / 1e3)
+        for v in range(len(w.nodes)):
+            S = st[node == v]
+            if not len(S):
+                continue
+            windows.setdefault(v, []).append(((S[:, 0].min() - t0) / 1e3, (S[:, 1].min() - t0) / 1e3,
+                                              (S[:, 9].max() - t0) / 1e3, len(S)))
+            used = [i for i in range(10) if (S[:, i] > 0).all()]
+            for a, b in zip(used[:-1], used[1:]):
+                phases.setdefault(v, {}).setdefault(f"{STAMPS[a]}->{STAMPS[b]}", []).extend(
+                    list((S[:, b] - S[:, a]) / 1e3))
+    out = []
+    for v in sorted(windows):
+        win = np.median(np.array(windows[v]), axis=0)
+        n = w.nodes[v]
+        out.append({"kernel": v, "name": getattr(n, "name", "") or f"{n.op}{v}", "op": n.op,
+                    "tiles": int(win[3]), "first_claim_us": round(float(win[0]), 2),
+                    "first_ready_us": round(float(win[1]), 2), "last_release_us": round(float(win[2]), 2),
+                    "phase_median_us": {k: round(float(np.median(x)), 2) for k, x in phases[v].items()}})
+    return {"traced_launch_us_median": round(float(np.median(spans)), 2), "kernels": out}
 
 
 def make_workload(name):
@@ -610,9 +655,9 @@ def main():
     X_ids = [i for i in w.input_ids() if i not in weights]
     Y_ids = w.output_ids()
 
-    def make_dag(streamed, fuse=0):
+    def make_dag(streamed, fuse=0, trace=0):
         o = options(use_graph=1 if batched else 0, f32_gemm=abi.DAG_F32_GEMM_SIMT if args.f32_simt else 0,
-                    fuse=fuse)
+                    fuse=fuse, trace=trace)
         if batched:
             return Dag.batch(wl, o, resident_inputs=not streamed, streamed=set(X_ids) if streamed else None)
         return Dag(w, o, streamed=set(X_ids)) if streamed else Dag(w, o, resident_inputs=True)
@@ -656,6 +701,17 @@ def main():
     if args.profile:
         print(json.dumps({"profile_run": True, "median_us": statistics.median(fine_us)}))
         d.close()
+        return 0
+    if args.timeline:
+        dt = make_dag(False, trace=1)
+        dt.set_inputs(ins)
+        for _ in range(max(3, args.warmup)):
+            dt.run()
+        tl = run_timeline(args, w, dt, abi, stream, flush)
+        dt.close()
+        d.close()
+        print(json.dumps({"timeline": args.workload, "config": {"workload": desc},
+                          "untraced_makespan_us_median": round(statistics.median(fine_us), 2), **tl}))
         return 0
     coarse_us, _ = timed(d.submit_coarse, max(3, args.steps // 4) if batched else max(10, args.steps // 4), 3)
     # kernel-by-kernel launches: one per kernel not fused into a GEMM, two for a split GEMM

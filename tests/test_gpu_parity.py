@@ -12,7 +12,7 @@ import synth
 from paper_2009_07482_gb300 import _binding as abi
 from paper_2009_07482_gb300.dag import Dag, options
 from synth import BF16, F32
-from synth.workloads import Workload, branchy_mlp, encoder_block, fork_join, random_layered
+from synth.workloads import Workload, branchy_mlp, encoder_block, fork_join, from_arrays, random_layered
 from tests.gpu_util import bits_equal, check_trace, compare, run_gpu, written_buffers
 
 pytestmark = pytest.mark.gpu
@@ -40,6 +40,25 @@ def _roundtrip(w, opts=None, coarse_too=True):
         assert bits_equal(got, got_c), "coarse and fine paths differ"
     d.close()
     return errs
+
+
+def test_gelu_elementwise_accuracy():
+    """GELU (erf form) of every f32 on a dense grid over [-12, 12], element by
+    element against the FP64 oracle rounded to f32: within 4e-7 |x| (the
+    erf approximation's 1.5e-7 and a few ulp of f32 evaluation of the erfc
+    term, scaled by 0.5 |x|) plus two f32 spacings of the result."""
+    x = np.linspace(-12.0, 12.0, 512 * 1000).reshape(512, 1000)
+    w, ids = from_arrays("gelu_grid", {"x": (x, F32)})
+    y = w.buf(512, 1000, F32, "output")
+    w.node("unary", ids["x"], y, act="gelu")
+    ins = w.make_inputs()
+    ref = oracle.run(w, ins)[y]
+    got = run_gpu(w, ins)[y]
+    xx = ins[ids["x"]].astype(np.float64)
+    bound = 4e-7 * np.abs(xx) + 2 * np.spacing(np.abs(ref)).astype(np.float64)
+    err = np.abs(got.astype(np.float64) - ref.astype(np.float64))
+    assert np.all(err <= bound), float(np.max(err / bound))
+    assert got[-1, -1] == np.float32(12.0)
 
 
 @pytest.mark.parametrize("n", [256, 200, 64, 130])
