@@ -16,7 +16,8 @@ Also measured and reported on the same JSON line:
              from pinned memory, execution, readback of Y, every step
   roofline   the executor kernel's achieved TFLOP/s against the measured peak
   cp_roofline  makespan against the DAG's critical-path / total-work bounds
-  cpu_baseline the FP64 oracle on a bounded row sample, on the host cores
+  cpu_baseline the FP64 oracle on a bounded row sample, on one host core
+  cpu_baseline_all_cores  (MLP workloads) the same on every host core at once
 
 --impl reference times the FP64 oracle (the only reference implementation of
 this method) on the host cores instead.
@@ -334,6 +335,60 @@ def oracle_sample(workload):
     full, desc, _ = oracle_model(workload)
     n_dags = 256 if workload == "batched" else 1
     return {"value": n_dags / full, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+
+
+def _oracle_rows_proc(dt, ra, rb, barrier, out):
+    """One process of oracle_all_cores: build the samples, then time the oracle
+    on ra and on rb batch rows of the MLP, each start aligned with the others."""
+    import oracle
+    from synth.workloads import branchy_mlp
+    oracle.build()
+    wa, wb = branchy_mlp(dt, batch=ra), branchy_mlp(dt, batch=rb)
+    ia, ib = wa.make_inputs(), wb.make_inputs()
+    barrier.wait(timeout=300)
+    ta = _oracle_seconds(wa, ia)
+    barrier.wait(timeout=300)
+    tb = _oracle_seconds(wb, ib)
+    out.put((ta, tb))
+
+
+def oracle_all_cores(workload, ra=4, rb=12, procs=None):
+    """The FP64 oracle on every host core at once.  The MLP's batch rows are
+    independent, so a full DAG splits into one share of rows per core: each of
+    `procs` processes (spawned, so none inherits the parent's CUDA context)
+    times the same row samples as oracle_model at the same moment as the
+    others, and the slowest one gives the fixed part (each share widens the
+    weights once) and the per-row slope under all-core load.  One DAG then takes
+    fixed + ceil(512 / procs) * slope."""
+    import multiprocessing as mp
+    dt = "bf16" if workload == "mlp_bf16" else "f32"
+    P = procs or len(os.sched_getaffinity(0))
+    ctx = mp.get_context("spawn")
+    barrier, out = ctx.Barrier(P), ctx.Queue()
+    ps = [ctx.Process(target=_oracle_rows_proc, args=(dt, ra, rb, barrier, out)) for _ in range(P)]
+    for p in ps:
+        p.start()
+    import queue
+    res, deadline = [], time.time() + 420
+    try:
+        while len(res) < P:
+            try:
+                res.append(out.get(timeout=2))
+            except queue.Empty:
+                if any(p.exitcode not in (None, 0) for p in ps) or time.time() > deadline:
+                    raise RuntimeError("a worker process of the all-cores oracle timing failed or ran too long")
+    finally:
+        for p in ps:
+            p.join(timeout=5)
+            if p.is_alive():
+                p.terminate()
+    ta, tb = max(r[0] for r in res), max(r[1] for r in res)
+    slope = max(tb - ta, 0.0) / (rb - ra)
+    rows = -(-512 // P)
+    full = max(ta - ra * slope, 0.0) + rows * slope
+    return {"value": 1.0 / full, "unit": UNIT, "cores": P, "kind": "oracle",
+            "sample": (f"branchy MLP {dt}: {P} processes at once, each on {ra} and {rb} batch rows "
+                       f"(slowest {ta:.2f} s, {tb:.2f} s); one DAG = fixed part + {rows} rows per process")}
 
 
 def run_reference(args):
@@ -860,6 +915,11 @@ def main():
         line["learned"] = learned_eval_batched(wl, ins, abi, Dag, options, timed_fn)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(args.workload)
+        if args.workload.startswith("mlp"):
+            try:
+                line["cpu_baseline_all_cores"] = oracle_all_cores(args.workload)
+            except Exception as e:  # a host-side extra: never costs the measured line
+                line["cpu_baseline_all_cores"] = {"unavailable": str(e)[:200]}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

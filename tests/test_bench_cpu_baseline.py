@@ -1,0 +1,21 @@
+"""bench.py's all-cores oracle baseline: spawned processes, each timing the
+oracle on its own batch rows at the same moment (CPU only, two processes)."""
+import bench
+
+
+def test_all_cores_baseline_runs_and_reports_its_processes():
+    r = bench.oracle_all_cores("mlp_bf16", ra=1, rb=2, procs=2)
+    assert r["cores"] == 2 and r["kind"] == "oracle" and r["unit"] == bench.UNIT
+    assert 0 < r["value"] < 100          # DAGs/s of a float64 CPU executor on 512 rows
+    assert "2 processes" in r["sample"] and "256 rows per process" in r["sample"]
+
+
+def test_a_failing_worker_is_reported_not_waited_for():
+    import time
+
+    import pytest
+
+    t0 = time.time()
+    with pytest.raises(RuntimeError, match="failed or ran too long"):
+        bench.oracle_all_cores("mlp_bf16", ra=0, rb=1, procs=2)    # a 0-row DAG: the oracle rejects it
+    assert time.time() - t0 < 120
