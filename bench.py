@@ -344,7 +344,8 @@ def _oracle_rows_proc(dt, ra, rb, barrier, out):
     from synth.workloads import branchy_mlp
     oracle.build()
     wa, wb = branchy_mlp(dt, batch=ra), branchy_mlp(dt, batch=rb)
-    ia, ib = wa.make_inputs(), wb.make_inputs()
+    cache = {}                              # both samples share one draw of the weights
+    ia, ib = wa.make_inputs(cache), wb.make_inputs(cache)
     barrier.wait(timeout=300)
     ta = _oracle_seconds(wa, ia)
     barrier.wait(timeout=300)
@@ -352,17 +353,19 @@ def _oracle_rows_proc(dt, ra, rb, barrier, out):
     out.put((ta, tb))
 
 
-def oracle_all_cores(workload, ra=4, rb=12, procs=None):
+def oracle_all_cores(workload, ra=4, rb=20, procs=None):
     """The FP64 oracle on every host core at once.  The MLP's batch rows are
     independent, so a full DAG splits into one share of rows per core: each of
     `procs` processes (spawned, so none inherits the parent's CUDA context)
     times the same row samples as oracle_model at the same moment as the
-    others, and the slowest one gives the fixed part (each share widens the
-    weights once) and the per-row slope under all-core load.  One DAG then takes
-    fixed + ceil(512 / procs) * slope."""
+    others; from its two samples each extrapolates the time of its share of a
+    DAG, fixed + ceil(512 / procs) * slope (each share widens the weights once),
+    under all-core load.  The shares are alike, so a DAG takes the median share
+    (the slowest one would mostly measure timing noise).  At most 64 processes
+    (about 0.3 GB each)."""
     import multiprocessing as mp
     dt = "bf16" if workload == "mlp_bf16" else "f32"
-    P = procs or len(os.sched_getaffinity(0))
+    P = procs or min(len(os.sched_getaffinity(0)), 64)
     ctx = mp.get_context("spawn")
     barrier, out = ctx.Barrier(P), ctx.Queue()
     ps = [ctx.Process(target=_oracle_rows_proc, args=(dt, ra, rb, barrier, out)) for _ in range(P)]
@@ -382,13 +385,18 @@ def oracle_all_cores(workload, ra=4, rb=12, procs=None):
             p.join(timeout=5)
             if p.is_alive():
                 p.terminate()
-    ta, tb = max(r[0] for r in res), max(r[1] for r in res)
-    slope = max(tb - ta, 0.0) / (rb - ra)
     rows = -(-512 // P)
-    full = max(ta - ra * slope, 0.0) + rows * slope
+
+    def share(ta, tb):  # one process's share of a DAG, from its own two samples
+        slope = max(tb - ta, 0.0) / (rb - ra)
+        return max(ta - ra * slope, 0.0) + rows * slope
+
+    shares = sorted(share(ta, tb) for ta, tb in res)
+    full = shares[len(shares) // 2]   # the processes are alike: the median share, robust to timing noise
     return {"value": 1.0 / full, "unit": UNIT, "cores": P, "kind": "oracle",
-            "sample": (f"branchy MLP {dt}: {P} processes at once, each on {ra} and {rb} batch rows "
-                       f"(slowest {ta:.2f} s, {tb:.2f} s); one DAG = fixed part + {rows} rows per process")}
+            "sample": (f"branchy MLP {dt}: {P} processes at once, each timing {ra} and {rb} batch rows and "
+                       f"extrapolating its share of {rows} rows ({shares[0]:.1f} to {shares[-1]:.1f} s); "
+                       f"one DAG = the median share")}
 
 
 def run_reference(args):

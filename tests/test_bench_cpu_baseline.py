@@ -7,7 +7,7 @@ def test_all_cores_baseline_runs_and_reports_its_processes():
     r = bench.oracle_all_cores("mlp_bf16", ra=1, rb=2, procs=2)
     assert r["cores"] == 2 and r["kind"] == "oracle" and r["unit"] == bench.UNIT
     assert 0 < r["value"] < 100          # DAGs/s of a float64 CPU executor on 512 rows
-    assert "2 processes" in r["sample"] and "256 rows per process" in r["sample"]
+    assert "2 processes" in r["sample"] and "share of 256 rows" in r["sample"]
 
 
 def test_a_failing_worker_is_reported_not_waited_for():
