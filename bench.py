@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--timeline", action="store_true",
                     help="diagnostic: per-kernel phases of traced launches (claim, dependencies, K loop, epilogue, "
                          "release) instead of the measured line")
+    ap.add_argument("--chrome-trace", metavar="PATH", default=None,
+                    help="with --timeline: also write the last traced launch as a Chrome trace-event file")
     return ap.parse_args()
 
 
@@ -771,6 +773,8 @@ def main():
         for _ in range(max(3, args.warmup)):
             dt.run()
         tl = run_timeline(args, w, dt, abi, stream, flush)
+        if args.chrome_trace:
+            dt.write_chrome_trace(args.chrome_trace)
         dt.close()
         d.close()
         print(json.dumps({"timeline": args.workload, "config": {"workload": desc},

@@ -133,6 +133,13 @@ class Dag:
     def trace(self):
         return abi.dag_trace_get(self.h)
 
+    def write_chrome_trace(self, path: str) -> None:
+        """The last traced submit as a Chrome trace-event file (a Gantt chart per
+        SM; needs options(trace=1)).  See trace.py."""
+        from .trace import write_chrome_trace
+        names = [n.name or f"{n.op}{i}" for i, n in enumerate(self.w.nodes)]
+        write_chrome_trace(path, self.trace(), names)
+
     def tiles(self):
         return abi.dag_tiles_get(self.h)
 
