@@ -17,7 +17,10 @@ marshalling and bookkeeping only; forward, backward and Adam run on the GPU.
 """
 from __future__ import annotations
 
+import hashlib
+import json
 import math
+import subprocess
 from typing import Dict, List, Optional, Sequence
 
 import numpy as np
@@ -177,6 +180,36 @@ class CostModel:
         counts = np.bincount(tiles[:, 0], minlength=len(w.nodes))
         return node_costs_from_tile_times(self.predict_tile_us(F), counts, info.grid)
 
+    # -- checkpoints -------------------------------------------------------
+    def save(self, path: str, device: Optional[Dict] = None) -> None:
+        """Weights, feature normalisation and the device they were trained on
+        (tile times are only meaningful on the GPU and clocks they came from)."""
+        meta = {"format": CHECKPOINT_FORMAT, "n_features": N_FEATURES, "hidden": 64,
+                "device": device if device is not None else device_info()}
+        with open(path, "wb") as f:
+            np.savez(f, params=abi.dag_mlp_get_params(self.h), mu=self.mu, sd=self.sd,
+                     meta=np.frombuffer(json.dumps(meta).encode(), np.uint8))
+
+    @classmethod
+    def load(cls, path: str, device: Optional[Dict] = None, any_device: bool = False) -> "CostModel":
+        """A model saved by save(); refuses one trained on another GPU model or
+        SM count unless any_device (clocks are recorded, not compared: they
+        vary from run to run)."""
+        with np.load(path) as z:
+            meta = json.loads(z["meta"].tobytes().decode())
+            params, mu, sd = z["params"], z["mu"], z["sd"]
+        if meta.get("format") != CHECKPOINT_FORMAT or meta.get("n_features") != N_FEATURES:
+            raise ValueError(f"{path}: not a cost-model checkpoint of this version")
+        if not any_device:
+            check_same_device(meta.get("device", {}), device if device is not None else device_info(), path)
+        m = cls()
+        if params.size != abi.dag_mlp_param_count(m.h):
+            m.close()
+            raise ValueError(f"{path}: {params.size} parameters, the network has {abi.dag_mlp_param_count(m.h)}")
+        abi.dag_mlp_set_params(m.h, params)
+        m.mu, m.sd = mu.astype(np.float32), sd.astype(np.float32)
+        return m
+
     def close(self):
         if self.h:
             abi.dag_mlp_destroy(self.h)
@@ -187,6 +220,81 @@ class CostModel:
             self.close()
         except Exception:
             pass
+
+
+CHECKPOINT_FORMAT = 1
+
+
+def device_info(ordinal: int = 0) -> Dict:
+    """What a recorded time depends on: the GPU model, its SM count and its
+    maximum SM clock (from nvidia-smi, if it answers)."""
+    info = {"gpu": "none", "sms": 0, "sm_max_mhz": None}
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pr = torch.cuda.get_device_properties(ordinal)
+            info["gpu"], info["sms"] = pr.name, int(pr.multi_processor_count)
+    except Exception:
+        pass
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(ordinal), "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=10)
+        if out.returncode == 0 and out.stdout.strip():
+            info["sm_max_mhz"] = float(out.stdout.strip().splitlines()[0])
+    except Exception:
+        pass
+    return info
+
+
+def check_same_device(saved: Dict, current: Dict, what: str) -> None:
+    if saved.get("gpu") != current.get("gpu") or saved.get("sms") != current.get("sms"):
+        raise ValueError(f"{what}: recorded on {saved.get('gpu')} ({saved.get('sms')} SMs), "
+                         f"this is {current.get('gpu')} ({current.get('sms')} SMs)")
+
+
+def dag_signature(w) -> str:
+    """A DAG's identity for a profile: every buffer's shape, dtype, role and
+    view, and every kernel's operation, operands and attributes."""
+    h = hashlib.sha256()
+    for b in w.buffers:
+        h.update(repr((b.rows, b.cols, b.dtype, b.role, b.view_of, b.col_offset)).encode())
+    for n in w.nodes:
+        h.update(repr((n.op, n.a, n.b, n.bias, n.out, n.trans_b, n.act, float(n.scale), n.batch)).encode())
+    return h.hexdigest()[:32]
+
+
+class ProfileDB:
+    """Measured per-kernel costs (profile_costs) of DAGs, by signature, saved
+    to and loaded from a JSON file that records the device they came from."""
+
+    def __init__(self, device: Optional[Dict] = None):
+        self.device = device if device is not None else device_info()
+        self.costs: Dict[str, List[float]] = {}
+
+    def record(self, w, costs: Sequence[float]) -> None:
+        if len(costs) != len(w.nodes):
+            raise ValueError(f"{len(costs)} costs for {len(w.nodes)} kernels")
+        self.costs[dag_signature(w)] = [float(c) for c in costs]
+
+    def get(self, w) -> Optional[List[float]]:
+        return self.costs.get(dag_signature(w))
+
+    def save(self, path: str) -> None:
+        with open(path, "w") as f:
+            json.dump({"format": CHECKPOINT_FORMAT, "device": self.device, "costs": self.costs}, f)
+
+    @classmethod
+    def load(cls, path: str, device: Optional[Dict] = None, any_device: bool = False) -> "ProfileDB":
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("format") != CHECKPOINT_FORMAT:
+            raise ValueError(f"{path}: not a profile database of this version")
+        cur = device if device is not None else device_info()
+        if not any_device:
+            check_same_device(d.get("device", {}), cur, path)
+        db = cls(d.get("device", cur))
+        db.costs = {k: [float(c) for c in v] for k, v in d.get("costs", {}).items()}
+        return db
 
 
 def mape(pred: np.ndarray, true: np.ndarray) -> float:
