@@ -121,3 +121,39 @@ def test_trace_check_catches_an_epilogue_that_did_not_wait():
     # without the fusion map the trace is not even complete (K3 has no tiles)
     with pytest.raises(AssertionError):
         trace_check.check(w, t[:, :5], t[:, 5] >> 16, start, end)
+
+
+def _split_plan():
+    """The branchy MLP's host plan: its last GEMM is split in K (partials store
+    sums, a finishing partial adds them and writes the region)."""
+    w = branchy_mlp(BF16)
+    n, e, b = dagmod.describe(w, resident_inputs=True)
+    t, _ = abi.dag_plan_host(n, e, b, None, 148)
+    split = t[:, 5] >> 16
+    S, idx = split & 0xFF, split >> 8
+    assert (S > 1).any()
+    start = np.arange(len(t), dtype=np.int64) * 2    # tiles one at a time, in queue order
+    return w, t, split, S, idx, start
+
+
+def test_trace_check_split_k_violations_are_caught():
+    w, t, split, S, idx, start = _split_plan()
+    trace_check.check(w, t[:, :5], split, start, start + 1)          # legal
+    fin = np.nonzero((S > 1) & (idx == S - 1))[0][0]
+    region = tuple(t[fin, [0, 1, 3]])
+    part = next(i for i in np.nonzero((S > 1) & (idx < S - 1))[0] if tuple(t[i, [0, 1, 3]]) == region)
+    # (1) the finishing partial starts before a partial of its region has ended
+    s1, e1 = start.copy(), start + 1
+    s1[fin], e1[fin] = e1[part] - 1, e1[part] + 1
+    with pytest.raises(AssertionError, match="ends after its finishing tile"):
+        trace_check.check(w, t[:, :5], split, s1, e1)
+    # (2) a partial starts before a tile producing its A rows has released them
+    node = w.nodes[t[part, 0]]
+    pa = next(v for v, x in enumerate(w.nodes) if x.out == node.a)
+    prod = [i for i in range(len(t)) if t[i, 0] == pa and t[i, 1] < t[part, 2] and t[part, 1] < t[i, 2]]
+    assert prod
+    s2, e2 = start.copy(), start + 1
+    s2[part] = e2[prod[-1]] - 1
+    assert s2[part] < e2[part]
+    with pytest.raises(AssertionError, match="illegal trace"):
+        trace_check.check(w, t[:, :5], split, s2, e2)
