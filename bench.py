@@ -17,7 +17,8 @@ Also measured and reported on the same JSON line:
   roofline   the executor kernel's achieved TFLOP/s against the measured peak
   cp_roofline  makespan against the DAG's critical-path / total-work bounds
   cpu_baseline the FP64 oracle on a bounded row sample, on one host core
-  cpu_baseline_all_cores  (MLP workloads) the same on every host core at once
+  cpu_baseline_all_cores  the same on every host core at once (workloads whose
+             rows, sequences or heads are independent)
 
 --impl reference times the FP64 oracle (the only reference implementation of
 this method) on the host cores instead.
@@ -265,12 +266,47 @@ def load_peaks():
 _INPUTS = {}
 
 
-def _oracle_seconds(w, ins, repeat=1):
+def _oracle_seconds(w, ins, repeat=1, min_s=0.5):
+    """Mean seconds of one oracle run of w.  A run shorter than min_s counts as
+    a warm-up, and the timed runs are repeated until they add up to min_s."""
     import oracle
     t0 = time.perf_counter()
-    for _ in range(repeat):
+    oracle.run(w, ins)
+    t = time.perf_counter() - t0
+    if t >= min_s and repeat == 1:
+        return t
+    n = max(repeat, -(-min_s // max(t, 1e-6)))
+    t0 = time.perf_counter()
+    for _ in range(int(n)):
         oracle.run(w, ins)
-    return (time.perf_counter() - t0) / repeat
+    return (time.perf_counter() - t0) / n
+
+
+# workloads whose oracle sample is one of `units` independent parts of the DAG
+UNIT_SAMPLES = ("encoder", "heads", "softmax", "add")
+
+
+def unit_sample(workload):
+    """(sample workload, units per DAG, description) for UNIT_SAMPLES."""
+    from synth.workloads import Workload, encoder_block, transformer_heads
+    if workload == "encoder":
+        return encoder_block(batch=1), 8, "encoder block: 1 of 8 independent sequences (all 99 kernels)"
+    if workload == "heads":
+        return transformer_heads(1, 256), 16, "transformer heads: 1 of 16 independent heads (7 kernels)"
+    if workload == "softmax":
+        w = Workload("one_head_softmax")
+        a = w.buf(2048, 256, "f32", "input", ("uniform", 100), "S0")
+        w.node("softmax", a, w.buf(2048, 256, "bf16", "output"), scale=0.125)
+        return w, 16, "softmax level: 1 of 16 heads"
+    if workload == "add":
+        w = Workload("add_tree_rows")
+        xs = [w.buf(256, 4096, "bf16", "input", ("uniform", 200 + i)) for i in range(4)]
+        s0, s1 = w.buf(256, 4096, "bf16"), w.buf(256, 4096, "bf16")
+        w.node("add", xs[0], s0, b=xs[1])
+        w.node("add", xs[2], s1, b=xs[3])
+        w.node("add", s0, w.buf(256, 4096, "bf16", "output"), b=s1)
+        return w, 16, "add tree: 256 of 4096 rows"
+    raise ValueError(workload)
 
 
 def oracle_model(workload, ra=4, rb=12):
@@ -296,28 +332,10 @@ def oracle_model(workload, ra=4, rb=12):
         w = fork_join(256)
         t = _oracle_seconds(w, w.make_inputs(), repeat=3)
         return t, "fork-join 256^3 f32: the whole DAG, mean of 3 runs", (w, 256, t, 0.0)
-    if workload == "softmax":
-        from synth.workloads import Workload
-        w = Workload("one_head_softmax")
-        a = w.buf(2048, 256, "f32", "input", ("uniform", 100), "S0")
-        w.node("softmax", a, w.buf(2048, 256, "bf16", "output"), scale=0.125)
+    if workload in UNIT_SAMPLES:
+        w, units, what = unit_sample(workload)
         t = _oracle_seconds(w, w.make_inputs(_INPUTS))
-        return 16 * t, f"softmax level: 1 of 16 heads ({t:.2f} s), times 16", (w, 1, t, 0.0)
-    if workload == "add":
-        from synth.workloads import Workload
-        w = Workload("add_tree_rows")
-        xs = [w.buf(256, 4096, "bf16", "input", ("uniform", 200 + i)) for i in range(4)]
-        s0, s1 = w.buf(256, 4096, "bf16"), w.buf(256, 4096, "bf16")
-        w.node("add", xs[0], s0, b=xs[1])
-        w.node("add", xs[2], s1, b=xs[3])
-        w.node("add", s0, w.buf(256, 4096, "bf16", "output"), b=s1)
-        t = _oracle_seconds(w, w.make_inputs(_INPUTS))
-        return 16 * t, f"add tree: 256 of 4096 rows ({t:.2f} s), times 16", (w, 1, t, 0.0)
-    if workload == "heads":
-        from synth.workloads import transformer_heads
-        w = transformer_heads(1, 256)
-        t = _oracle_seconds(w, w.make_inputs(_INPUTS))
-        return 16 * t, f"transformer heads: 1 of 16 independent heads (7 kernels, {t:.2f} s), times 16", (w, 1, t, 0.0)
+        return units * t, f"{what} ({t:.2f} s), times {units}", (w, 1, t, 0.0)
     if workload == "batched":
         from synth.workloads import random_batch
         ws = random_batch(256)
@@ -328,9 +346,7 @@ def oracle_model(workload, ra=4, rb=12):
         scale = sum(flops) / max(1.0, sum(flops[i] for i in pick))
         return (t * scale, f"random batch: DAGs {pick} whole ({t:.2f} s), scaled by total GEMM flops (x{scale:.0f})",
                 (None, 0, t, 0.0))
-    w = encoder_block(batch=1)
-    t = _oracle_seconds(w, w.make_inputs())
-    return 8 * t, f"encoder block: 1 of 8 independent sequences (all 99 kernels, {t:.2f} s), times 8", (w, 1, t, 0.0)
+    raise ValueError(f"no oracle sample for workload {workload}")
 
 
 def oracle_sample(workload):
@@ -340,8 +356,8 @@ def oracle_sample(workload):
 
 
 def _oracle_rows_proc(dt, ra, rb, barrier, out):
-    """One process of oracle_all_cores: build the samples, then time the oracle
-    on ra and on rb batch rows of the MLP, each start aligned with the others."""
+    """One process of oracle_all_cores (MLP): build the samples, then time the
+    oracle on ra and on rb batch rows, each start aligned with the others."""
     import oracle
     from synth.workloads import branchy_mlp
     oracle.build()
@@ -355,25 +371,28 @@ def _oracle_rows_proc(dt, ra, rb, barrier, out):
     out.put((ta, tb))
 
 
-def oracle_all_cores(workload, ra=4, rb=20, procs=None):
-    """The FP64 oracle on every host core at once.  The MLP's batch rows are
-    independent, so a full DAG splits into one share of rows per core: each of
-    `procs` processes (spawned, so none inherits the parent's CUDA context)
-    times the same row samples as oracle_model at the same moment as the
-    others; from its two samples each extrapolates the time of its share of a
-    DAG, fixed + ceil(512 / procs) * slope (each share widens the weights once),
-    under all-core load.  The shares are alike, so a DAG takes the median share
-    (the slowest one would mostly measure timing noise).  At most 64 processes
-    (about 0.3 GB each)."""
+def _oracle_unit_proc(workload, barrier, out):
+    """One process of oracle_all_cores (UNIT_SAMPLES): time the oracle on one
+    independent part of the DAG, the start aligned with the others."""
+    import oracle
+    oracle.build()
+    w, _, _ = unit_sample(workload)
+    ins = w.make_inputs()
+    barrier.wait(timeout=300)
+    out.put(_oracle_seconds(w, ins))
+
+
+def _spawn_timed(target, args, P):
+    """Run target(*args, barrier, queue) in P spawned processes (none inherits
+    the parent's CUDA context) and return what each put on the queue; a process
+    that fails or stalls raises instead of hanging the caller."""
     import multiprocessing as mp
-    dt = "bf16" if workload == "mlp_bf16" else "f32"
-    P = procs or min(len(os.sched_getaffinity(0)), 64)
+    import queue
     ctx = mp.get_context("spawn")
     barrier, out = ctx.Barrier(P), ctx.Queue()
-    ps = [ctx.Process(target=_oracle_rows_proc, args=(dt, ra, rb, barrier, out)) for _ in range(P)]
+    ps = [ctx.Process(target=target, args=(*args, barrier, out)) for _ in range(P)]
     for p in ps:
         p.start()
-    import queue
     res, deadline = [], time.time() + 420
     try:
         while len(res) < P:
@@ -387,18 +406,47 @@ def oracle_all_cores(workload, ra=4, rb=20, procs=None):
             p.join(timeout=5)
             if p.is_alive():
                 p.terminate()
-    rows = -(-512 // P)
+    return res
 
-    def share(ta, tb):  # one process's share of a DAG, from its own two samples
-        slope = max(tb - ta, 0.0) / (rb - ra)
-        return max(ta - ra * slope, 0.0) + rows * slope
 
-    shares = sorted(share(ta, tb) for ta, tb in res)
-    full = shares[len(shares) // 2]   # the processes are alike: the median share, robust to timing noise
-    return {"value": 1.0 / full, "unit": UNIT, "cores": P, "kind": "oracle",
-            "sample": (f"branchy MLP {dt}: {P} processes at once, each timing {ra} and {rb} batch rows and "
-                       f"extrapolating its share of {rows} rows ({shares[0]:.1f} to {shares[-1]:.1f} s); "
-                       f"one DAG = the median share")}
+def oracle_all_cores(workload, ra=4, rb=20, procs=None):
+    """The FP64 oracle on every host core at once (at most 64 processes, about
+    0.3 GB each), from the same bounded samples as oracle_model, all started
+    together so that they share the machine as a parallel run would.
+
+    MLP: the batch rows are independent, so a DAG splits into one share of rows
+    per core; each process times ra and rb rows and extrapolates its share,
+    fixed + ceil(512 / procs) * slope (each share widens the weights once).
+    UNIT_SAMPLES: the sample is one of `units` independent parts (a sequence, a
+    head, a row block); min(procs, units) processes each time one, and a DAG
+    takes ceil(units / processes) of them.  The processes are alike, so the
+    median time stands for them (the slowest would mostly measure noise)."""
+    P = procs or min(len(os.sched_getaffinity(0)), 64)
+    if workload.startswith("mlp"):
+        dt = "bf16" if workload == "mlp_bf16" else "f32"
+        res = _spawn_timed(_oracle_rows_proc, (dt, ra, rb), P)
+        rows = -(-512 // P)
+
+        def share(ta, tb):  # one process's share of a DAG, from its own two samples
+            slope = max(tb - ta, 0.0) / (rb - ra)
+            return max(ta - ra * slope, 0.0) + rows * slope
+
+        shares = sorted(share(ta, tb) for ta, tb in res)
+        full = shares[len(shares) // 2]
+        sample = (f"branchy MLP {dt}: {P} processes at once, each timing {ra} and {rb} batch rows and "
+                  f"extrapolating its share of {rows} rows ({shares[0]:.1f} to {shares[-1]:.1f} s); "
+                  f"one DAG = the median share")
+    elif workload in UNIT_SAMPLES:
+        _, units, what = unit_sample(workload)
+        P = min(P, units)
+        ts = sorted(_spawn_timed(_oracle_unit_proc, (workload,), P))
+        waves = -(-units // P)
+        full = ts[len(ts) // 2] * waves
+        sample = (f"{what}: {P} processes at once, each timing one part ({ts[0]:.2f} to {ts[-1]:.2f} s); "
+                  f"one DAG = {waves} x the median")
+    else:
+        raise ValueError(f"no all-cores oracle sample for workload {workload}")
+    return {"value": 1.0 / full, "unit": UNIT, "cores": P, "kind": "oracle", "sample": sample}
 
 
 def run_reference(args):
@@ -927,7 +975,7 @@ def main():
         line["learned"] = learned_eval_batched(wl, ins, abi, Dag, options, timed_fn)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(args.workload)
-        if args.workload.startswith("mlp"):
+        if args.workload.startswith("mlp") or args.workload in UNIT_SAMPLES:
             try:
                 line["cpu_baseline_all_cores"] = oracle_all_cores(args.workload)
             except Exception as e:  # a host-side extra: never costs the measured line

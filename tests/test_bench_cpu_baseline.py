@@ -19,3 +19,12 @@ def test_a_failing_worker_is_reported_not_waited_for():
     with pytest.raises(RuntimeError, match="failed or ran too long"):
         bench.oracle_all_cores("mlp_bf16", ra=0, rb=1, procs=2)    # a 0-row DAG: the oracle rejects it
     assert time.time() - t0 < 120
+
+
+def test_all_cores_baseline_of_independent_parts():
+    # the softmax level: one head of 16 per process; two processes take 8 heads each
+    r = bench.oracle_all_cores("softmax", procs=2)
+    assert r["cores"] == 2 and r["value"] > 0
+    assert "2 processes" in r["sample"] and "one DAG = 8 x the median" in r["sample"]
+    # never more processes than parts: the encoder's 8 sequences
+    assert bench.unit_sample("encoder")[1] == 8
