@@ -309,6 +309,17 @@ def unit_sample(workload):
     raise ValueError(workload)
 
 
+def batch_sample():
+    """The 256-DAG batch, the three DAGs with the least GEMM work (the bounded
+    sample, run whole) and the factor that scales their time to the batch (the
+    ratio of GEMM flops)."""
+    from synth.workloads import random_batch
+    ws = random_batch(256)
+    flops = [sum(x.node_flops(k) for k, n in enumerate(x.nodes) if n.op == "gemm") for x in ws]
+    pick = sorted(range(len(ws)), key=lambda i: flops[i])[:3]
+    return ws, pick, sum(flops) / max(1.0, sum(flops[i] for i in pick))
+
+
 def oracle_model(workload, ra=4, rb=12):
     """Seconds per full DAG of the FP64 oracle on one host core, from a bounded
     sample.  MLP / fork-join rows are independent, so the time is
@@ -337,13 +348,8 @@ def oracle_model(workload, ra=4, rb=12):
         t = _oracle_seconds(w, w.make_inputs(_INPUTS))
         return units * t, f"{what} ({t:.2f} s), times {units}", (w, 1, t, 0.0)
     if workload == "batched":
-        from synth.workloads import random_batch
-        ws = random_batch(256)
-        flops = [sum(x.node_flops(k) for k, n in enumerate(x.nodes) if n.op == "gemm") for x in ws]
-        # the three DAGs with the least GEMM work, whole, scaled by total work
-        pick = sorted(range(len(ws)), key=lambda i: flops[i])[:3]
+        ws, pick, scale = batch_sample()
         t = sum(_oracle_seconds(ws[i], ws[i].make_inputs(_INPUTS)) for i in pick)
-        scale = sum(flops) / max(1.0, sum(flops[i] for i in pick))
         return (t * scale, f"random batch: DAGs {pick} whole ({t:.2f} s), scaled by total GEMM flops (x{scale:.0f})",
                 (None, 0, t, 0.0))
     raise ValueError(f"no oracle sample for workload {workload}")
@@ -380,6 +386,16 @@ def _oracle_unit_proc(workload, barrier, out):
     ins = w.make_inputs()
     barrier.wait(timeout=300)
     out.put(_oracle_seconds(w, ins))
+
+
+def _oracle_batch_proc(barrier, out):
+    """One process of oracle_all_cores (batched): time the batch's sample."""
+    import oracle
+    oracle.build()
+    ws, pick, _ = batch_sample()
+    ins = {i: ws[i].make_inputs() for i in pick}
+    barrier.wait(timeout=300)
+    out.put(sum(_oracle_seconds(ws[i], ins[i]) for i in pick))
 
 
 def _spawn_timed(target, args, P):
@@ -419,8 +435,10 @@ def oracle_all_cores(workload, ra=4, rb=20, procs=None):
     fixed + ceil(512 / procs) * slope (each share widens the weights once).
     UNIT_SAMPLES: the sample is one of `units` independent parts (a sequence, a
     head, a row block); min(procs, units) processes each time one, and a DAG
-    takes ceil(units / processes) of them.  The processes are alike, so the
-    median time stands for them (the slowest would mostly measure noise)."""
+    takes ceil(units / processes) of them.  Batched: every process times the
+    batch's three-DAG sample, and the batch, scaled by GEMM flops, spreads over
+    the processes.  The processes are alike, so the median time stands for them
+    (the slowest would mostly measure noise)."""
     P = procs or min(len(os.sched_getaffinity(0)), 64)
     if workload.startswith("mlp"):
         dt = "bf16" if workload == "mlp_bf16" else "f32"
@@ -444,6 +462,12 @@ def oracle_all_cores(workload, ra=4, rb=20, procs=None):
         full = ts[len(ts) // 2] * waves
         sample = (f"{what}: {P} processes at once, each timing one part ({ts[0]:.2f} to {ts[-1]:.2f} s); "
                   f"one DAG = {waves} x the median")
+    elif workload == "batched":
+        _, pick, scale = batch_sample()
+        ts = sorted(_spawn_timed(_oracle_batch_proc, (), P))
+        full = ts[len(ts) // 2] * scale / P / 256          # per DAG, the batch's DAGs spread over P cores
+        sample = (f"random batch: {P} processes at once, each timing DAGs {pick} whole ({ts[0]:.2f} to "
+                  f"{ts[-1]:.2f} s); the batch = the median x {scale:.0f} (GEMM flops) / {P} processes")
     else:
         raise ValueError(f"no all-cores oracle sample for workload {workload}")
     return {"value": 1.0 / full, "unit": UNIT, "cores": P, "kind": "oracle", "sample": sample}
@@ -975,7 +999,7 @@ def main():
         line["learned"] = learned_eval_batched(wl, ins, abi, Dag, options, timed_fn)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(args.workload)
-        if args.workload.startswith("mlp") or args.workload in UNIT_SAMPLES:
+        if args.workload.startswith("mlp") or args.workload in UNIT_SAMPLES or batched:
             try:
                 line["cpu_baseline_all_cores"] = oracle_all_cores(args.workload)
             except Exception as e:  # a host-side extra: never costs the measured line

@@ -28,3 +28,11 @@ def test_all_cores_baseline_of_independent_parts():
     assert "2 processes" in r["sample"] and "one DAG = 8 x the median" in r["sample"]
     # never more processes than parts: the encoder's 8 sequences
     assert bench.unit_sample("encoder")[1] == 8
+
+
+def test_all_cores_baseline_of_the_batch():
+    one = bench.oracle_model("batched")[0]                  # seconds for the whole batch on one core
+    r = bench.oracle_all_cores("batched", procs=2)
+    assert r["cores"] == 2 and "/ 2 processes" in r["sample"]
+    # two cores at most halve the batch's time, and timing noise aside do not lose to one core
+    assert 256 / one * 0.5 < r["value"] < 256 / one * 2.6
