@@ -133,6 +133,26 @@ class Dag:
     def trace(self):
         return abi.dag_trace_get(self.h)
 
+    def write_cq_chrome_trace(self, path: str, n_queues: int = 1, components: int = abi.DAG_TC_WHOLE,
+                              fifo: int = 0):
+        """Run the paper's Alg. 1 on streams (run_cq) and write each kernel's
+        window as a Chrome trace-event file, one process per task component
+        (the Gantt view of the paper's §6).  Returns the dag_cq_result."""
+        import json
+        from .trace import kernel_windows_trace
+        r, ts, te = self.run_cq(n_queues=n_queues, components=components, fifo=fifo, times=True)
+        n = len(self.w.nodes)
+        if components == abi.DAG_TC_GIVEN:
+            groups = [getattr(x, "component", 0) for x in self.w.nodes]
+        elif components == abi.DAG_TC_WHOLE:
+            groups = [0] * n
+        else:
+            groups = list(range(n))
+        names = [x.name or f"{x.op}{i}" for i, x in enumerate(self.w.nodes)]
+        with open(path, "w") as f:
+            json.dump(kernel_windows_trace(ts, te, names, groups), f)
+        return r
+
     def write_chrome_trace(self, path: str) -> None:
         """The last traced submit as a Chrome trace-event file (a Gantt chart per
         SM; needs options(trace=1)).  See trace.py."""

@@ -14,6 +14,9 @@ SM with two rows,
 
 Events of one row never overlap: a tile's bar is cut where the next tile of
 the same row begins (the uncut times stay in the event's args).
+
+kernel_windows_trace does the same for whole-kernel windows, such as those
+of the paper's own Alg. 1 on CUDA streams.
 """
 from __future__ import annotations
 
@@ -66,3 +69,36 @@ def chrome_trace(records: Sequence, names: Optional[Sequence[str]] = None) -> Di
 def write_chrome_trace(path: str, records: Sequence, names: Optional[Sequence[str]] = None) -> None:
     with open(path, "w") as f:
         json.dump(chrome_trace(records, names), f)
+
+
+def kernel_windows_trace(start_us: Sequence[float], end_us: Sequence[float], names: Sequence[str],
+                         groups: Optional[Sequence[int]] = None, group_label: str = "component") -> Dict:
+    """Trace-event JSON of whole-kernel windows, as the paper's Gantt charts of
+    its schedules (§6): e.g. the [start, end) of each kernel under the paper's
+    Alg. 1 on streams (dag_submit_cq with per-kernel times).  One process per
+    group (task component); inside it, kernels are packed in start order onto
+    the first lane free at their start, so a lane never holds two kernels at
+    once and the lanes show the concurrency the queues achieved.  Kernels
+    without a window (end <= start, e.g. fused into another) are skipped."""
+    n = len(names)
+    groups = list(groups) if groups is not None else [0] * n
+    lanes: Dict[int, List[float]] = {}            # group -> end time of each lane
+    events = []
+    for v in sorted(range(n), key=lambda v: (float(start_us[v]), v)):
+        s, e = float(start_us[v]), float(end_us[v])
+        if not e > s:
+            continue
+        g = int(groups[v])
+        ends = lanes.setdefault(g, [])
+        lane = next((i for i, t in enumerate(ends) if t <= s), len(ends))
+        if lane == len(ends):
+            ends.append(e)
+        else:
+            ends[lane] = e
+        events.append({"name": names[v], "ph": "X", "pid": g, "tid": lane, "ts": s, "dur": e - s,
+                       "args": {"kernel": v}})
+    for g in sorted(lanes):
+        events.append({"name": "process_name", "ph": "M", "pid": g, "args": {"name": f"{group_label} {g}"}})
+        for i in range(len(lanes[g])):
+            events.append({"name": "thread_name", "ph": "M", "pid": g, "tid": i, "args": {"name": f"lane {i}"}})
+    return {"traceEvents": events, "displayTimeUnit": "ns"}

@@ -44,3 +44,18 @@ def test_rows_per_sm_times_and_no_overlap(tmp_path):
 
 def test_empty_trace():
     assert chrome_trace([])["traceEvents"] == []
+
+
+def test_kernel_windows_pack_into_non_overlapping_lanes():
+    from paper_2009_07482_gb300.trace import kernel_windows_trace
+    # component 0: k0 [0,10) and k1 [2,6) overlap -> two lanes; k2 [6,9) reuses lane 1;
+    # component 1: k3 [10,20); k4 has no window (fused into another kernel) and is skipped
+    start = [0.0, 2.0, 6.0, 10.0, 5.0]
+    end = [10.0, 6.0, 9.0, 20.0, 5.0]
+    tr = kernel_windows_trace(start, end, ["k0", "k1", "k2", "k3", "k4"], groups=[0, 0, 0, 1, 1])
+    ev = {e["name"]: e for e in tr["traceEvents"] if e["ph"] == "X"}
+    assert set(ev) == {"k0", "k1", "k2", "k3"}
+    assert [(ev[k]["pid"], ev[k]["tid"], ev[k]["ts"], ev[k]["dur"]) for k in ("k0", "k1", "k2", "k3")] == [
+        (0, 0, 0.0, 10.0), (0, 1, 2.0, 4.0), (0, 1, 6.0, 3.0), (1, 0, 10.0, 10.0)]
+    lanes = [e for e in tr["traceEvents"] if e["ph"] == "M" and e["name"] == "thread_name"]
+    assert sorted((e["pid"], e["tid"]) for e in lanes) == [(0, 0), (0, 1), (1, 0)]
