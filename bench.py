@@ -1,27 +1,36 @@
 #!/usr/bin/env python3
 """Benchmark: DAG makespan and DAGs/s of the fine-grained persistent executor.
 
-Default workload: the branchy MLP inference DAG (batch 512, four branches of
-three Linear(2048,2048)+bias+ReLU layers, pairwise add tree, Linear(2048,4096)
-+ReLU, Linear(4096,1024)), bf16 inputs with f32 accumulation, synthetic seeded
-inputs.  One step = one submission of the whole DAG (one persistent kernel
-launch), weights and activations resident in HBM; L2 is flushed (a 256 MiB
-write) between timed steps, outside the timed events.
+Default workload: the batched configuration, 256 seeded random layered DAGs
+(8-64 nodes, layer widths 1-8; GEMM 70% / elementwise 20% / softmax 10%;
+M, N, K in {64..2048}; bf16 or f32 per DAG) in one persistent launch replayed
+from a captured CUDA graph.  One step = one submission of the whole batch,
+weights and activations resident in HBM; L2 is flushed (a 256 MiB write)
+between timed steps, outside the timed events.
 
 Also measured and reported on the same JSON line:
   coarse     the same tiles launched kernel by kernel on one stream
   epilogue_fusion  the persistent executor with the opt-in epilogue fusion
-             modes, when the DAG has kernels they would fuse
-  e2e        the same metric through the C ABI with host buffers: upload of X
-             from pinned memory, execution, readback of Y, every step
+             modes, when the DAG has kernels they would fuse (single DAGs)
+  e2e        the same metric through the C ABI with host buffers: upload of
+             the activations from pinned memory, execution, readback of every
+             sink, every step
   roofline   the executor kernel's achieved TFLOP/s against the measured peak
   cp_roofline  makespan against the DAG's critical-path / total-work bounds
-  cpu_baseline the FP64 oracle on a bounded row sample, on one host core
-  cpu_baseline_all_cores  the same on every host core at once (workloads whose
-             rows, sequences or heads are independent)
+  learned    (batched) makespan under the learned, profiled and roofline
+             ranks and FIFO order
+  configs    (batched, one GPU) the single-DAG configurations measured the
+             same way: fork-join 256^3 f32 (the paper's Fig. 1), branchy MLP
+             bf16 and f32, encoder block bf16 -- makespan, kernel-by-kernel,
+             the paper's Alg. 1 on streams at its best queue count, and the
+             fractions of the critical-path and work bounds
+  cpu_baseline the FP64 oracle on a bounded sample, on one host core
+  cpu_baseline_all_cores  the same on every host core at once
 
 --impl reference times the FP64 oracle (the only reference implementation of
-this method) on the host cores instead.
+this method) on the host cores instead: each step runs whole units of the
+workload (a block of batch rows, a sequence, a head, rows of several DAGs of
+the batch) and the rate is the units done over the time spent.
 """
 from __future__ import annotations
 
@@ -46,11 +55,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mlp_bf16",
+    ap.add_argument("--workload", default="batched",
                     choices=["mlp_bf16", "mlp_f32", "fork_join", "encoder", "heads", "softmax", "add", "batched",
                              "serving", "exp1"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="batched: skip the cost-model comparison")
+    ap.add_argument("--no-configs", action="store_true", help="batched: skip the single-DAG configurations")
     ap.add_argument("--profile", action="store_true", help="few steps, no side measurements (for ncu)")
     ap.add_argument("--f32-simt", action="store_true", help="f32 GEMMs on the SM cores (FFMA) instead of 3 x TF32")
     ap.add_argument("--timeline", action="store_true",
@@ -309,15 +319,55 @@ def unit_sample(workload):
     raise ValueError(workload)
 
 
-def batch_sample():
-    """The 256-DAG batch, the three DAGs with the least GEMM work (the bounded
-    sample, run whole) and the factor that scales their time to the batch (the
-    ratio of GEMM flops)."""
+def _row_subset(w, ins, rows):
+    """The DAG w restricted to batch rows `rows` of every row-space buffer
+    (the random layered DAGs and the MLPs are row-wise: row i of every kernel
+    output depends on row i of its row-space inputs and on whole weights),
+    with its inputs: the oracle on it computes exactly those rows."""
+    import dataclasses
+    weights = {n.b for n in w.nodes if n.op == "gemm"} | {n.bias for n in w.nodes if n.op == "gemm" and n.bias >= 0}
+    rs = {i for i, b in enumerate(w.buffers) if b.role != "input" or i not in weights}
+    ws = w.clone()
+    for i in rs:
+        ws.buffers[i] = dataclasses.replace(ws.buffers[i], rows=len(rows))
+    return ws, {i: (a[rows] if i in rs else a) for i, a in ins.items()}
+
+
+def _gemm_flops(w):
+    return sum(w.node_flops(k) for k, n in enumerate(w.nodes) if n.op == "gemm")
+
+
+BATCH_ROWS = 4
+
+
+def batch_sample(stride=8, first=0):
+    """The 256-DAG batch and a bounded sample of it: the first BATCH_ROWS rows
+    of every `stride`-th DAG (from `first`), each run whole over those rows.
+    Returns (DAGs, picked ids, GEMM flops of the sample, GEMM flops of the
+    batch); all work of these DAGs is row-wise, so the sample's share of the
+    batch's work is the ratio of GEMM flops."""
     from synth.workloads import random_batch
     ws = random_batch(256)
-    flops = [sum(x.node_flops(k) for k, n in enumerate(x.nodes) if n.op == "gemm") for x in ws]
-    pick = sorted(range(len(ws)), key=lambda i: flops[i])[:3]
-    return ws, pick, sum(flops) / max(1.0, sum(flops[i] for i in pick))
+    pick = list(range(first, len(ws), stride))
+    rows = BATCH_ROWS
+    f_sample = sum(sum(w.node_flops(k) * rows / w.buffers[n.a].rows for k, n in enumerate(w.nodes) if n.op == "gemm")
+                   for w in (ws[i] for i in pick))
+    return ws, pick, f_sample, sum(_gemm_flops(x) for x in ws)
+
+
+def _batch_sample_seconds(ws, pick, inputs=None):
+    """Seconds of the oracle on the batch sample (inputs drawn beforehand)."""
+    import numpy as np
+    import oracle
+    rows = np.arange(BATCH_ROWS)
+    subs = []
+    for i in pick:
+        ins = inputs[i] if inputs else ws[i].make_inputs()
+        subs.append(_row_subset(ws[i], ins, rows))
+    t0 = time.perf_counter()
+    for w, ins in subs:
+        oracle.run(w, ins)
+    return time.perf_counter() - t0
 
 
 def oracle_model(workload, ra=4, rb=12):
@@ -348,9 +398,11 @@ def oracle_model(workload, ra=4, rb=12):
         t = _oracle_seconds(w, w.make_inputs(_INPUTS))
         return units * t, f"{what} ({t:.2f} s), times {units}", (w, 1, t, 0.0)
     if workload == "batched":
-        ws, pick, scale = batch_sample()
-        t = sum(_oracle_seconds(ws[i], ws[i].make_inputs(_INPUTS)) for i in pick)
-        return (t * scale, f"random batch: DAGs {pick} whole ({t:.2f} s), scaled by total GEMM flops (x{scale:.0f})",
+        ws, pick, f_s, f_b = batch_sample()
+        t = _batch_sample_seconds(ws, pick)
+        return (t * f_b / f_s / 256,
+                f"random batch: the first {BATCH_ROWS} rows of each of {len(pick)} DAGs (every 8th) in {t:.2f} s; "
+                f"extrapolated to the batch by GEMM flops (x{f_b / f_s:.0f}), per DAG = the batch / 256",
                 (None, 0, t, 0.0))
     raise ValueError(f"no oracle sample for workload {workload}")
 
@@ -392,10 +444,10 @@ def _oracle_batch_proc(barrier, out):
     """One process of oracle_all_cores (batched): time the batch's sample."""
     import oracle
     oracle.build()
-    ws, pick, _ = batch_sample()
+    ws, pick, _, _ = batch_sample()
     ins = {i: ws[i].make_inputs() for i in pick}
     barrier.wait(timeout=300)
-    out.put(sum(_oracle_seconds(ws[i], ins[i]) for i in pick))
+    out.put(_batch_sample_seconds(ws, pick, ins))
 
 
 def _spawn_timed(target, args, P):
@@ -463,20 +515,63 @@ def oracle_all_cores(workload, ra=4, rb=20, procs=None):
         sample = (f"{what}: {P} processes at once, each timing one part ({ts[0]:.2f} to {ts[-1]:.2f} s); "
                   f"one DAG = {waves} x the median")
     elif workload == "batched":
-        _, pick, scale = batch_sample()
+        _, pick, f_s, f_b = batch_sample()
         ts = sorted(_spawn_timed(_oracle_batch_proc, (), P))
-        full = ts[len(ts) // 2] * scale / P / 256          # per DAG, the batch's DAGs spread over P cores
-        sample = (f"random batch: {P} processes at once, each timing DAGs {pick} whole ({ts[0]:.2f} to "
-                  f"{ts[-1]:.2f} s); the batch = the median x {scale:.0f} (GEMM flops) / {P} processes")
+        full = ts[len(ts) // 2] * (f_b / f_s) / P / 256    # per DAG, the batch's DAGs spread over P cores
+        sample = (f"random batch: {P} processes at once, each timing the first {BATCH_ROWS} rows of each of "
+                  f"{len(pick)} DAGs ({ts[0]:.2f} to {ts[-1]:.2f} s); the batch = the median x {f_b / f_s:.0f} "
+                  f"(GEMM flops) / {P} processes")
     else:
         raise ValueError(f"no all-cores oracle sample for workload {workload}")
     return {"value": 1.0 / full, "unit": UNIT, "cores": P, "kind": "oracle", "sample": sample}
 
 
+def reference_units(workload, step):
+    """Whole units of work for the reference arm's step `step`: a list of
+    (oracle workload, its inputs) plus the fraction of one DAG of the
+    benchmark's workload they make up, and a description.  Inputs are drawn
+    here, before the step's timer starts."""
+    from synth.workloads import branchy_mlp, fork_join
+    if workload.startswith("mlp"):
+        rows = 64
+        w = branchy_mlp("bf16" if workload == "mlp_bf16" else "f32", batch=rows)
+        return [(w, w.make_inputs(_INPUTS))], rows / 512, f"a block of {rows} of the 512 batch rows (all 17 kernels)"
+    if workload == "fork_join":
+        w = fork_join(256)
+        return [(w, w.make_inputs(_INPUTS))], 1.0, "the whole DAG"
+    if workload in UNIT_SAMPLES:
+        w, units, what = unit_sample(workload)
+        return [(w, w.make_inputs(_INPUTS))], 1.0 / units, what
+    if workload == "batched":
+        import numpy as np
+        ws, _, _, f_b = _REF_BATCH or _ref_batch()
+        k0 = (8 * step) % 256
+        units, f = [], 0.0
+        for k in range(k0, k0 + 8):
+            w = ws[k]
+            units.append(_row_subset(w, w.make_inputs(), np.arange(BATCH_ROWS)))
+            f += sum(w.node_flops(j) * BATCH_ROWS / w.buffers[n.a].rows for j, n in enumerate(w.nodes) if n.op == "gemm")
+        return units, f / (f_b / 256), (f"the first {BATCH_ROWS} rows of 8 DAGs of the batch (DAGs 8s..8s+7 at "
+                                        f"step s), counted in DAGs of the batch's mean GEMM work")
+    raise ValueError(workload)
+
+
+_REF_BATCH = None
+
+
+def _ref_batch():
+    global _REF_BATCH
+    _REF_BATCH = batch_sample()
+    return _REF_BATCH
+
+
 def run_reference(args):
-    """The FP64 oracle as the reference arm: each step runs a bounded sample of
-    the workload on one host core and is scaled to one full DAG with the
-    calibration of oracle_model (measured once before the steps)."""
+    """The FP64 oracle as the reference arm, on one host core: every step
+    runs whole units of the workload (see reference_units) and is timed as
+    it ran; the rate is the DAG fraction those units make up, summed over the
+    timed steps, over the time they took.  Nothing is extrapolated into the
+    timed figures; the full-DAG time the rate implies is reported beside them
+    under its own name."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
@@ -484,46 +579,31 @@ def run_reference(args):
         print(json.dumps({"impl": "reference", "unavailable": f"--workload {args.workload} has no oracle arm; "
                           "its DAGs are timed in the other workloads"}))
         return 0
+    import oracle
+    oracle.build()
     _, desc = make_workload(args.workload)
-    full, cal_desc, (w, rows, t_cal, slope) = oracle_model(args.workload)
-    if args.workload.startswith("mlp"):
-        from synth.workloads import branchy_mlp
-        rows = 1
-        w = branchy_mlp("bf16" if args.workload == "mlp_bf16" else "f32", batch=rows)
-    if w is None:  # batched: the calibration run is the step
-        per = [full] * args.steps
-        ms = full * 1e3
-        line = {"impl": "reference", "metric": METRIC, "value": 1e3 / ms * 256, "unit": UNIT, "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
-                "config": {"workload": desc, "parallelism": "host oracle, rank 0 only"},
-                "cpu_baseline": {"value": 1e3 / ms * 256, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                 "sample": cal_desc},
-                "e2e": {"value": 1e3 / ms * 256, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(line))
-        return 0
-    ins = w.make_inputs(_INPUTS)
-    scale_rows = 512 if args.workload.startswith("mlp") else None
-    per = []
+    per, frac = [], []
+    what = ""
     for i in range(args.warmup + args.steps):
-        t = _oracle_seconds(w, ins)
-        if scale_rows:
-            t = t + (scale_rows - rows) * slope
-        elif args.workload == "encoder":
-            t = 8 * t
-        elif args.workload in ("heads", "softmax", "add"):
-            t = 16 * t
+        units, f, what = reference_units(args.workload, i)
+        t0 = time.perf_counter()
+        for w, ins in units:
+            oracle.run(w, ins)
+        t = time.perf_counter() - t0
         if i >= args.warmup:
             per.append(t)
+            frac.append(f)
+    rate = sum(frac) / sum(per)
     ms = statistics.mean(per) * 1e3
-    what = f"{rows} batch row(s)" if scale_rows else cal_desc.split(" (")[0]
-    sample = f"each step: the oracle on {what}, scaled to one full DAG; calibration: {cal_desc}"
-    line = {"impl": "reference", "metric": METRIC, "value": 1e3 / ms, "unit": UNIT, "n_gpus": args.gpus,
+    sample = f"each step: the oracle on {what}; rate = DAG fraction done / time spent over the timed steps"
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
             "config": {"workload": desc, "parallelism": "host oracle, rank 0 only"},
-            "cpu_baseline": {"value": 1e3 / ms, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
-            "e2e": {"value": 1e3 / ms, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "dag_fraction_per_step": statistics.mean(frac),
+            "implied_seconds_per_full_dag": 1.0 / rate,
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
@@ -751,6 +831,102 @@ def run_serving(args):
     return 0
 
 
+def roofline_of(w, info, mean_us, peaks, peaks_src, f32_simt):
+    """Roofline of one executor launch of workload w taking mean_us: achieved
+    TFLOP/s (GB/s for a DAG without GEMMs) against the measured peak of the
+    arithmetic the GEMMs run in.  f32 GEMMs: the larger of the FP32 ALU peak
+    (152 SMs x 128 FFMA/clk x 2 flop x max SM clock) and the 3 x TF32 tensor
+    peak (measured bf16 x the nominal tf32/bf16 ratio 1.1/2.25, / 3
+    products); the executor runs them on the tensor cores unless f32_simt.
+    A DAG with both takes the flop-weighted peak.  Returns (roof, flops by
+    dtype)."""
+    simt_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    tc_peak = peaks["bf16_tflops"] * (1.1 / 2.25) / 3.0
+    f32_peak = simt_peak if f32_simt else max(simt_peak, tc_peak)
+    fl = {"bf16": 0.0, "f32": 0.0}
+    for k, n in enumerate(w.nodes):
+        if n.op == "gemm":
+            fl[w.buffers[n.a].dtype] += w.node_flops(k)
+    t_bound_us = (fl["bf16"] / peaks["bf16_tflops"] + fl["f32"] / f32_peak) / 1e6
+    achieved = info.flops / (mean_us * 1e-6) / 1e12
+    src_bf16 = f"{peaks_src} bf16 burst (MEASURED_PEAKS.json)" if peaks_src == "measured" else "fallback 1.9 PF/s"
+    src_f32 = ("3 x TF32 on the tensor cores: measured bf16 burst x 1.1/2.25 (nominal tf32/bf16) / 3"
+               if f32_peak == tc_peak else "derived: 152 SMs x 128 f32 FMA/clk x 2 flop x max SM clock")
+    if fl["f32"] == 0 and fl["bf16"] == 0:  # no GEMM: the DAG is bound by HBM bandwidth
+        roof = {"bound": "hbm", "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "peak_source": f"{peaks_src} HBM copy bandwidth (MEASURED_PEAKS.json)"}
+    elif fl["f32"] == 0:
+        roof = {"bound": "tensor", "peak": peaks["bf16_tflops"], "peak_source": src_bf16}
+    elif fl["bf16"] == 0:
+        roof = {"bound": "alu" if f32_simt else "tensor", "peak": f32_peak, "peak_source": src_f32}
+    else:
+        roof = {"bound": "tensor", "peak": info.flops / t_bound_us / 1e6,
+                "peak_source": f"flop-weighted: bf16 at {src_bf16}, f32 at {src_f32}"}
+    if roof["bound"] == "hbm":
+        achieved = info.bytes / (mean_us * 1e-6) / 1e9
+        roof.update({"achieved": achieved, "frac": achieved / roof["peak"]})
+    else:
+        roof.update({"achieved": achieved, "unit": "TFLOP/s", "frac": achieved / roof["peak"]})
+    return roof, fl
+
+
+CONFIGS = ("fork_join", "mlp_bf16", "mlp_f32", "encoder")
+
+
+def config_extras(args, abi, Dag, options, stream, flush, peaks, peaks_src, reps=20):
+    """The single-DAG configurations, each measured as the main line measures
+    its workload (inputs resident, L2 flushed between steps, CUDA events on
+    the launching stream): device makespan of the persistent executor, the
+    kernel-by-kernel path, the paper's Alg. 1 on streams (given components,
+    q = 1..5, best), and the fractions of the critical-path and work bounds
+    and of the measured peak."""
+    import torch
+    sp = stream.cuda_stream
+    out = {}
+
+    def timed(submit, dd, n):
+        for _ in range(3):
+            submit(sp)
+            abi.check(dd.wait(), "wait")
+        ts = []
+        for _ in range(n):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            submit(sp)
+            b.record(stream)
+            abi.check(dd.wait(), "wait")
+            ts.append(a.elapsed_time(b) * 1e3)
+        return ts
+
+    for name in CONFIGS:
+        w, desc = make_workload(name)
+        d = Dag(w, options(), resident_inputs=True)
+        d.set_inputs(w.make_inputs(_INPUTS))
+        d.run()
+        fine = timed(d.submit, d, max(reps, args.steps))
+        coarse = timed(d.submit_coarse, d, max(5, reps // 2))
+        alg1 = paper_alg1(d, abi, reps=5)
+        info = d.plan()
+        med = statistics.median(fine)
+        roof, _ = roofline_of(w, info, statistics.mean(fine), peaks, peaks_src, False)
+        out[name] = {"workload": desc, "tiles": info.n_tiles,
+                     "makespan_us": {"median": med, "mean": statistics.mean(fine), "min": min(fine)},
+                     "dags_per_s": 1e6 / statistics.mean(fine),
+                     "coarse_us": statistics.median(coarse),
+                     "speedup_fine_over_coarse": statistics.median(coarse) / med,
+                     "paper_alg1": {"best_q": alg1["best_q"], "best_us": alg1["best_us"],
+                                    "eager_us": alg1["eager_us"],
+                                    "speedup_persistent_over_best": alg1["best_us"] / med},
+                     "cp_roofline": {"critical_path_us": info.critical_path_us, "work_bound_us": info.work_bound_us,
+                                     "frac_of_cp": info.critical_path_us / med,
+                                     "frac_of_work_bound": info.work_bound_us / med},
+                     "roofline": {k: roof[k] for k in ("bound", "achieved", "peak", "unit", "frac")}}
+        d.close()
+        _INPUTS.clear()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -852,7 +1028,7 @@ def main():
         print(json.dumps({"timeline": args.workload, "config": {"workload": desc},
                           "untraced_makespan_us_median": round(statistics.median(fine_us), 2), **tl}))
         return 0
-    coarse_us, _ = timed(d.submit_coarse, max(3, args.steps // 4) if batched else max(10, args.steps // 4), 3)
+    coarse_us, _ = timed(d.submit_coarse, min(10, max(3, args.steps // 4)) if batched else max(10, args.steps // 4), 3)
     # kernel-by-kernel launches: one per kernel not fused into a GEMM, two for a split GEMM
     fused = d.fusion()
     tl = d.tiles()
@@ -860,7 +1036,7 @@ def main():
     n_coarse_launches = sum(1 + (v in split_nodes) for v in range(len(w.nodes)) if fused[v] < 0)
     # the opt-in epilogue-fusion modes (the measured line runs without fusion)
     unfused = None
-    for name, mode in (("activations", abi.DAG_FUSE_ACT), ("activations_and_adds", abi.DAG_FUSE_ALL)):
+    for name, mode in (() if batched else (("activations", abi.DAG_FUSE_ACT), ("activations_and_adds", abi.DAG_FUSE_ALL))):
         fo = options(fuse=mode, f32_gemm=abi.DAG_F32_GEMM_SIMT if args.f32_simt else 0)
         n_f = sum(h >= 0 for h in abi.dag_fusion_host(*describe(w, resident_inputs=True), fo))
         if not n_f:
@@ -904,7 +1080,7 @@ def main():
         abi.check(e.wait(), "wait")
     barrier()
     t0 = time.perf_counter()
-    e2e_steps = args.steps if not batched else max(3, args.steps // 4)
+    e2e_steps = args.steps if not batched else min(10, max(3, args.steps // 4))
     for _ in range(e2e_steps):
         e.submit(sp)
         abi.check(e.wait(), "wait")
@@ -918,37 +1094,7 @@ def main():
     e.close()
 
     # roofline of the executor kernel (the only kernel of a step)
-    # f32 GEMMs: the larger of the FP32 ALU peak (152 SMs x 128 FFMA/clk x 2
-    # flop x max SM clock) and the 3 x TF32 tensor peak (measured bf16 x the
-    # nominal tf32/bf16 ratio 1.1/2.25, / 3 products); the executor runs them
-    # on the tensor cores unless --f32-simt
-    simt_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    tc_peak = peaks["bf16_tflops"] * (1.1 / 2.25) / 3.0
-    f32_peak = simt_peak if args.f32_simt else max(simt_peak, tc_peak)
-    fl = {"bf16": 0.0, "f32": 0.0}
-    for k, n in enumerate(w.nodes):
-        if n.op == "gemm":
-            fl[w.buffers[n.a].dtype] += w.node_flops(k)
-    t_bound_us = (fl["bf16"] / peaks["bf16_tflops"] + fl["f32"] / f32_peak) / 1e6
-    achieved = info.flops / (mean_us * 1e-6) / 1e12
-    src_bf16 = f"{peaks_src} bf16 burst (MEASURED_PEAKS.json)" if peaks_src == "measured" else "fallback 1.9 PF/s"
-    src_f32 = ("3 x TF32 on the tensor cores: measured bf16 burst x 1.1/2.25 (nominal tf32/bf16) / 3"
-               if f32_peak == tc_peak else "derived: 152 SMs x 128 f32 FMA/clk x 2 flop x max SM clock")
-    if fl["f32"] == 0 and fl["bf16"] == 0:  # no GEMM: the DAG is bound by HBM bandwidth
-        roof = {"bound": "hbm", "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "peak_source": f"{peaks_src} HBM copy bandwidth (MEASURED_PEAKS.json)"}
-    elif fl["f32"] == 0:
-        roof = {"bound": "tensor", "peak": peaks["bf16_tflops"], "peak_source": src_bf16}
-    elif fl["bf16"] == 0:
-        roof = {"bound": "alu" if args.f32_simt else "tensor", "peak": f32_peak, "peak_source": src_f32}
-    else:
-        roof = {"bound": "tensor", "peak": info.flops / t_bound_us / 1e6,
-                "peak_source": f"flop-weighted: bf16 at {src_bf16}, f32 at {src_f32}"}
-    if roof["bound"] == "hbm":
-        achieved = info.bytes / (mean_us * 1e-6) / 1e9
-        roof.update({"achieved": achieved, "frac": achieved / roof["peak"]})
-    else:
-        roof.update({"achieved": achieved, "unit": "TFLOP/s", "frac": achieved / roof["peak"]})
+    roof, fl = roofline_of(w, info, mean_us, peaks, peaks_src, args.f32_simt)
     bf16 = fl["bf16"] > 0 and fl["f32"] == 0
     traffic, sha = traffic_for(args.workload)
     roof["traffic"] = traffic
@@ -997,6 +1143,8 @@ def main():
                 out.append(a.elapsed_time(b) * 1e3)
             return out
         line["learned"] = learned_eval_batched(wl, ins, abi, Dag, options, timed_fn)
+    if batched and world == 1 and not args.no_configs:
+        line["configs"] = config_extras(args, abi, Dag, options, stream, flush, peaks, peaks_src)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(args.workload)
         if args.workload.startswith("mlp") or args.workload in UNIT_SAMPLES or batched:

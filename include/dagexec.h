@@ -165,11 +165,20 @@ typedef enum { DAG_F32_GEMM_TENSOR = 0, DAG_F32_GEMM_SIMT = 1 } dag_f32_gemm;
 typedef struct dag_handle dag_handle;
 
 /*
- * dag_create: validate the DAG (acyclic, one writer per element, shapes and
- * dtypes), tile every kernel, build the tile dependency counters, order the
- * tiles (a linear extension of the tile DAG ranked by the scheduler), and
- * allocate all device memory.  opts may be NULL.  *out receives the handle;
- * free it with dag_destroy.  Needs a CUDA device.
+ * dag_create: build the paper's DAG G = <(K,B),(E_I,E_O,E)> (§3, Problem
+ * Formulation) from the node, buffer and optional edge lists (edges in the
+ * k_i,b_r -> k_j,b_s form of §4.A, Design Frontend); validate it (acyclic,
+ * as a valid schedule requires a topological dispatch order, Def. 5; one
+ * writer per element; shapes and dtypes); tile every kernel; build the tile
+ * dependency counters (the precedence set E_Q of the command-queue structure,
+ * Def. 4 and its rules i-iii, taken from kernels down to output tiles); order
+ * the tiles (a linear extension of the tile DAG ranked by the bottom-level
+ * rank of §5, the priority of the task queue F in Alg. 1); and allocate all
+ * device memory.  opts may be NULL.  *out receives the handle; free it with
+ * dag_destroy.  Needs a CUDA device.
+ * Errors: DAG_EINVAL (bad id, count or edge not implied by the buffers),
+ * DAG_ECYCLE, DAG_ESHAPE, DAG_EDTYPE, DAG_EMULTIWRITER, DAG_EUNSUPPORTED,
+ * DAG_ENOMEM (device allocation), DAG_EDEVICE; *out is untouched on error.
  */
 dag_status dag_create(const dag_node_desc *nodes, int n_nodes, const dag_edge *edges, int n_edges,
                       const dag_buffer_desc *buffers, int n_buffers, const dag_options *opts,
@@ -194,7 +203,9 @@ dag_status dag_batch_create(const dag_batch_item *items, int n_items, const dag_
 
 /*
  * dag_set_input: give the host data of input buffer `buf` (rows x cols,
- * dense, its dtype: f32 or bf16 bit patterns).  The pointer is recorded, not
+ * dense, its dtype: f32 or bf16 bit patterns): the source of the isolated
+ * write (b_m, k) of §3 (an E_I edge with no producer), which Alg. 1's enq
+ * enqueues before the kernel's ndrange command.  The pointer is recorded, not
  * copied: it must stay valid and unchanged until the next dag_wait returns.
  * The copy runs at the next dag_submit on an upload stream (a copy engine)
  * that overlaps compute; tiles reading the buffer wait on its ready flag.
@@ -203,22 +214,31 @@ dag_status dag_batch_create(const dag_batch_item *items, int n_items, const dag_
 dag_status dag_set_input(dag_handle *h, int buf, const void *host_ptr);
 
 /* dag_set_output: host destination (rows x cols, dense) that every following
- * dag_submit fills after the kernel (device->host on a copy stream); NULL
- * cancels.  Same lifetime rule as dag_set_input.  DAG_EINVAL for a weight
+ * dag_submit fills after the kernel (device->host on a copy stream): the
+ * isolated read (k, b_n) of §3 (an E_O edge with no consumer), enqueued after
+ * the kernel's ndrange command (§3, the enq rules; Alg. 1); NULL cancels.  Same lifetime rule as dag_set_input.  DAG_EINVAL for a weight
  * kept transposed on the device (dag_options.keep_layout). */
 dag_status dag_set_output(dag_handle *h, int buf, void *host_ptr);
 
 /*
- * dag_submit: enqueue one execution: pending uploads on the upload streams
- * (each followed by its ready flag), one persistent executor launch on
- * `stream`, and registered readbacks.  Asynchronous; returns after enqueue.
- * DAG_EBUSY if the previous submit was not waited for.
+ * dag_submit: enqueue one execution of a valid schedule (Def. 5): pending
+ * uploads on the upload streams (each followed by its ready flag), one
+ * persistent executor launch on `stream`, and registered readbacks.  This is
+ * the device-side form of Alg. 1's dispatch loop (schedule / setup_cq /
+ * dispatch, with the callbacks cb replaced by dependency counters in device
+ * memory), at the granularity of output tiles instead of kernels: the
+ * sub-kernel interleaving named as future work in §7.  Asynchronous; returns
+ * after enqueue.  Errors: DAG_EBUSY if the previous submit was not waited
+ * for; DAG_EDEVICE if a copy or the launch could not be enqueued; the error
+ * of a poisoned handle.
  */
 dag_status dag_submit(dag_handle *h, void *stream);
 
-/* dag_submit_coarse: the coarse-grained baseline: uploads on `stream`, then
- * one launch per kernel in topological order on `stream` (the same tile code,
- * a grid of that kernel's tiles, no cross-kernel overlap), then readbacks.
+/* dag_submit_coarse: the coarse-grained baseline (§2, one command queue: each
+ * kernel's write, ndrange and read commands finish before the next kernel's;
+ * §6's default configuration): uploads on `stream`, then one launch per kernel
+ * in topological order on `stream` (the same tile code, a grid of that
+ * kernel's tiles, no cross-kernel overlap), then readbacks.
  * A GEMM with fused elementwise kernels launches in the place of the last of
  * them (DAG_FUSE_NONE gives one launch per kernel throughout). */
 dag_status dag_submit_coarse(dag_handle *h, void *stream);
@@ -274,8 +294,10 @@ typedef struct {
 dag_status dag_submit_cq(dag_handle *h, const dag_cq_options *opts, dag_cq_result *result);
 
 /* dag_wait: block until the last submit finished or timeout_ns passed
- * (DAG_ETIMEOUT, the submit stays in flight).  Then reads the device error
- * word: DAG_ETIMEOUT if a device wait ran out, DAG_EDEVICE on a CUDA error. */
+ * (DAG_ETIMEOUT, the submit stays in flight): the host side of Alg. 1's
+ * sleep_till_cb_update, which waits until every kernel of G has finished.
+ * Then reads the device error word: DAG_ETIMEOUT if a device wait ran out
+ * (the handle is poisoned), DAG_EDEVICE on a CUDA error. */
 dag_status dag_wait(dag_handle *h, uint64_t timeout_ns);
 
 /* dag_poll: non-blocking dag_wait: DAG_EBUSY while the last submit (with its
@@ -284,7 +306,10 @@ dag_status dag_poll(dag_handle *h);
 
 /* dag_get_output: synchronous device->host copy of buffer `buf` (rows x cols,
  * dense, the caller's layout even for a weight kept transposed on the
- * device) into host_ptr; call after dag_wait. */
+ * device) into host_ptr; call after dag_wait.  The on-demand form of the
+ * isolated read (k, b_n) of §3.  host_ptr is caller-owned and must hold
+ * rows x cols elements.  Errors: DAG_EINVAL (bad id or NULL pointer),
+ * DAG_EBUSY (a submit not yet waited for), DAG_EDEVICE. */
 dag_status dag_get_output(dag_handle *h, int buf, void *host_ptr);
 
 /* dag_device_ptr: device address of buffer `buf` (borrowed, valid until
@@ -292,7 +317,10 @@ dag_status dag_get_output(dag_handle *h, int buf, void *host_ptr);
  * weight kept transposed on the device (dag_options.keep_layout). */
 const void *dag_device_ptr(dag_handle *h, int buf, int64_t *ld_elems);
 
-/* dag_destroy: wait for outstanding work (bounded), free everything. */
+/* dag_destroy: wait for outstanding work (bounded), free everything the
+ * handle owns (device buffers, plan, streams, events); the handle is invalid
+ * afterwards.  The paper has no counterpart beyond releasing the OpenCL
+ * objects of §4.B; NULL is accepted (DAG_OK). */
 dag_status dag_destroy(dag_handle *h);
 
 /* dag_last_error: message of the last failure on this thread ("" if none). */
@@ -318,7 +346,10 @@ void dag_host_free(void *p);
  *     of every root buffer i (ignored for views, which live inside their
  *     parent).  Pitches must be >= cols and a multiple of 16 bytes; pointers
  *     16-byte aligned.  Inputs must already hold their data; outputs and
- *     intermediates are written in place.
+ *     intermediates are written in place.  No two root buffers may share an
+ *     element of device memory (an output placed on an input, say): the
+ *     planner treats roots as distinct objects, so overlapping roots are
+ *     rejected with DAG_EINVAL before any device work.
  *   The executor's own working state (tile queue, dependency counters, node
  *   parameters, TMA descriptors, control block) lives in a fixed 1 MiB device
  *   array that every GPU loading this library holds until process exit.  A

@@ -28,6 +28,7 @@
 #include <cstring>
 #include <mutex>
 #include <queue>
+#include <set>
 #include <string>
 #include <thread>
 #include <vector>
@@ -81,6 +82,8 @@ static PFN_cuTensorMapEncodeTiled_v12000 p_encode_tiled = nullptr;
 static PFN_cuStreamWriteValue32_v11070 p_write_value32 = nullptr;
 static std::once_flag g_driver_once;
 static std::string g_driver_err;
+static std::mutex g_prepared_mu;
+static std::set<int> g_prepared;  // device ordinals whose executor attributes are set
 
 static dag_status init_driver() {
   std::call_once(g_driver_once, [] {
@@ -93,9 +96,17 @@ static dag_status init_driver() {
                                          cudaEnableDefault, &q) != cudaSuccess ||
         q != cudaDriverEntryPointSuccess || !p_write_value32)
       g_driver_err = "cuStreamWriteValue32 not available";
-    if (g_driver_err.empty() && exec_prepare() != cudaSuccess) g_driver_err = "cudaFuncSetAttribute failed";
   });
   if (!g_driver_err.empty()) return fail(DAG_EDEVICE, "%s", g_driver_err.c_str());
+  // the executor's shared-memory attribute is set per device context: once
+  // for every device this process plans on, with that device current
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return fail(DAG_EDEVICE, "no current CUDA device");
+  std::lock_guard<std::mutex> lock(g_prepared_mu);
+  if (!g_prepared.count(dev)) {
+    if (exec_prepare() != cudaSuccess) return fail(DAG_EDEVICE, "cudaFuncSetAttribute failed on device %d", dev);
+    g_prepared.insert(dev);
+  }
   return DAG_OK;
 }
 

@@ -9,6 +9,8 @@
 // counters, node parameters, TMA descriptors and control block -- in one
 // fixed array below, which every GPU that loads this library holds from
 // module load until process exit.
+#include <algorithm>
+#include <cstdio>
 #include <mutex>
 #include <vector>
 
@@ -28,12 +30,60 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 char *g_scratch[kMaxDevices] = {};
 
+// Root buffers are distinct objects to the planner (one writer per element,
+// dependency counters per buffer), so caller memory of two roots must not
+// share an element.  Each root covers rows of `cols` elements `pitch` apart;
+// two roots overlap when some row segment of one meets a row segment of the
+// other.  Checked before any device work (and with no device call).
+dag_status check_disjoint_roots(const dag_buffer_desc *b, int n, void *const *ptrs, const int64_t *lds) {
+  struct Span {
+    uint64_t p, end, pitch, width, rows;
+    int id;
+  };
+  std::vector<Span> sp;
+  for (int i = 0; i < n; ++i) {
+    if (b[i].view_of >= 0 || !ptrs[i] || lds[i] <= 0 || b[i].rows <= 0 || b[i].cols <= 0) continue;
+    const uint64_t es = b[i].dtype == DAG_BF16 ? 2 : 4;
+    const uint64_t p = (uint64_t)(uintptr_t)ptrs[i], pitch = (uint64_t)lds[i] * es, w = (uint64_t)b[i].cols * es;
+    sp.push_back(Span{p, p + (uint64_t)(b[i].rows - 1) * pitch + w, pitch, w, (uint64_t)b[i].rows, i});
+  }
+  std::sort(sp.begin(), sp.end(), [](const Span &x, const Span &y) { return x.p < y.p; });
+  for (size_t a = 0; a < sp.size(); ++a)
+    for (size_t c = a + 1; c < sp.size() && sp[c].p < sp[a].end; ++c) {
+      const Span &x = sp[a], &y = sp[c];
+      bool meet = true;
+      if (x.pitch == y.pitch && x.width <= x.pitch && y.width <= y.pitch) {
+        // row i of x starts at x.p + i L, row j of y at y.p + j L; with
+        // t = (y.p - x.p) + (j - i) L they meet iff -y.width < t < x.width,
+        // which only k = j - i = floor(-d / L) or that + 1 can satisfy
+        const int64_t L = (int64_t)x.pitch, d = (int64_t)(y.p - x.p);
+        const int64_t k0 = -((d + L - 1) / L);
+        meet = false;
+        for (int64_t k = k0; k <= k0 + 1 && !meet; ++k) {
+          if (k < -((int64_t)x.rows - 1) || k > (int64_t)y.rows - 1) continue;
+          const int64_t t = d + k * L;
+          meet = t > -(int64_t)y.width && t < (int64_t)x.width;
+        }
+      }
+      if (meet) {
+        char msg[128];
+        snprintf(msg, sizeof msg, "dag_run_noalloc: root buffers %d and %d overlap in device memory",
+                 std::min(x.id, y.id), std::max(x.id, y.id));
+        return dagx::report_error(DAG_EINVAL, msg);
+      }
+    }
+  return DAG_OK;
+}
+
 }  // namespace
 
 extern "C" dag_status dag_run_noalloc(const dag_node_desc *nodes, int n_nodes, const dag_buffer_desc *buffers,
                                       int n_buffers, void *const *buffer_ptrs, const int64_t *row_pitch,
                                       const dag_options *opts, void *stream_) {
   cudaStream_t stream = (cudaStream_t)stream_;
+  if (n_buffers > 0 && (!buffers || !buffer_ptrs || !row_pitch))
+    return dagx::report_error(DAG_EINVAL, "dag_run_noalloc: null buffer, pointer or pitch array");
+  if (dag_status s = check_disjoint_roots(buffers, n_buffers, buffer_ptrs, row_pitch)) return s;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return dagx::report_error(DAG_EDEVICE, "dag_run_noalloc: no usable current CUDA device");

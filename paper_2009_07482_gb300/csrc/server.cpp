@@ -220,6 +220,24 @@ static int progress_locked(dag_server *s) {
       free_slot = idle[r->model].back();
       idle[r->model].pop_back();
     } else if (!blocked_new) {
+      // evict only when evicting every idle slot of the other models would
+      // make room: otherwise warm slots would be torn down for nothing
+      if (!fits(r->model)) {
+        size_t freeable = 0;
+        int evictable = 0;
+        for (auto &sl : s->slots)
+          if (!sl.req && sl.model != r->model) {
+            freeable += s->models[sl.model].footprint;
+            ++evictable;
+          }
+        const bool room = (int)s->slots.size() - evictable < s->max_slots &&
+                          free_mem + freeable > s->reserve + s->models[r->model].footprint + (64u << 20);
+        if (!room) {
+          blocked_new = true;
+          ++it;
+          continue;
+        }
+      }
       while (!fits(r->model)) {
         auto victim = s->slots.end();
         for (auto sit = s->slots.begin(); sit != s->slots.end(); ++sit)

@@ -214,3 +214,34 @@ def test_f32_gemm_tile_kind(a_off, mode):
             assert rows.max() == 128 and cols.max() == 64
         else:
             assert set(mine[:, 5].tolist()) <= {0, 1, 2}
+
+
+def _noalloc_status(bufs, ptrs, pitch):
+    nodes = [abi.dag_node_desc(abi.DAG_OP_ADD, 0, 1, -1, 2, 0, 0, 1.0, 1, 0)]
+    return abi.dag_run_noalloc(nodes, bufs, ptrs, pitch, None, 0)
+
+
+def test_no_alloc_rejects_overlapping_root_buffers():
+    """dag_run_noalloc: two root buffers sharing device memory (an output
+    placed on an input, or rows of one falling inside another) are rejected
+    with DAG_EINVAL before any device call; interleaved buffers whose rows
+    never meet, and disjoint ones, pass this check (and then, with no GPU
+    here, stop at the device query with DAG_EDEVICE)."""
+    f32 = abi.DAG_F32
+    bufs = [abi.dag_buffer_desc(4, 16, f32, abi.DAG_BUF_INPUT, -1, 0),
+            abi.dag_buffer_desc(4, 16, f32, abi.DAG_BUF_INPUT, -1, 0),
+            abi.dag_buffer_desc(4, 16, f32, abi.DAG_BUF_OUTPUT, -1, 0)]
+    base = 1 << 30
+    # the output on top of the first input
+    assert _noalloc_status(bufs, [base, base + 4096, base], [16, 16, 16]) == abi.DAG_EINVAL
+    assert "overlap" in abi.last_error()
+    # the output starting inside the second input's last row
+    assert _noalloc_status(bufs, [base, base + 4096, base + 4096 + 3 * 64 + 32], [16, 16, 16]) == abi.DAG_EINVAL
+    # three buffers interleaved column-wise in one allocation of pitch 48: rows never meet
+    assert _noalloc_status(bufs, [base, base + 64, base + 128], [48, 48, 48]) == abi.DAG_EDEVICE
+    # the same, but the second one 16 bytes too wide for its slot
+    wide = list(bufs)
+    wide[1] = abi.dag_buffer_desc(4, 20, f32, abi.DAG_BUF_INPUT, -1, 0)
+    assert _noalloc_status(wide, [base, base + 64, base + 128], [48, 48, 48]) == abi.DAG_EINVAL
+    # disjoint
+    assert _noalloc_status(bufs, [base, base + 4096, base + 8192], [16, 16, 16]) == abi.DAG_EDEVICE

@@ -33,4 +33,16 @@ def test_all_cores_baseline_of_independent_parts():
 def test_all_cores_baseline_of_the_batch():
     r = bench.oracle_all_cores("batched", procs=2)
     assert r["cores"] == 2 and r["value"] > 0
-    assert "/ 2 processes" in r["sample"] and "DAGs [" in r["sample"]
+    assert "/ 2 processes" in r["sample"] and "rows of each of 32 DAGs" in r["sample"]
+
+
+def test_reference_arm_times_whole_units():
+    """The reference arm's rate is the DAG fraction of the units it ran over
+    the time it spent: a step is whole units (here: rows of 8 DAGs of the
+    batch), and the batch's sample covers every DAG over 32 steps."""
+    units, f, what = bench.reference_units("batched", 0)
+    assert len(units) == 8 and 0 < f < 1 and "8 DAGs" in what
+    u2, f2, _ = bench.reference_units("batched", 32)
+    assert f2 == f                       # step 32 wraps to DAGs 0..7
+    units, f, _ = bench.reference_units("encoder", 0)
+    assert f == 1 / 8 and len(units) == 1

@@ -1,9 +1,12 @@
 """dag_run_noalloc: the entry point for callers that cannot allocate device
 memory (their device memory is fully reserved by their own pool, or they run
-inside an allocator or an error path).  It must give the same results as the
-dag_create / dag_submit path on the same DAG, on two calls in a row (the fixed
-working area is reused and must be cleared between calls), and it must turn
-away a DAG whose plan does not fit that fixed area.
+inside an allocator or an error path).  On two calls in a row (the fixed
+working area is reused and must be cleared between calls) it must give the
+same bits as the dag_create / dag_submit path planned the same way (no split
+K, the caller's weight layout), and values within the per-buffer tolerance
+of the FP64 oracle; it must accept caller row pitches wider than the
+library's own (with head outputs written as column slices of a wider
+buffer); and it must turn away a DAG whose plan does not fit that fixed area.
 
 This file is named so that pytest collects it last."""
 import numpy as np
@@ -11,7 +14,7 @@ import pytest
 
 import oracle
 from paper_2009_07482_gb300 import _binding as abi
-from paper_2009_07482_gb300.dag import describe
+from paper_2009_07482_gb300.dag import describe, options
 from synth import BF16, F32, storage_to_f64
 from synth.workloads import Workload, encoder_block, fork_join
 from tests.gpu_util import node_tolerance, run_gpu, written_buffers
@@ -26,9 +29,10 @@ def lib():
     abi.lib()
 
 
-def _caller_buffers(w, inputs):
+def _caller_buffers(w, inputs, extra=0):
     """Device buffers owned by the caller (this test), one per root buffer,
-    with a 16-element row pitch; inputs copied in."""
+    with a row pitch of round_up(cols, 16) + `extra` elements; inputs copied
+    in."""
     import torch
     tensors, ptrs, pitch = {}, [], []
     for i, b in enumerate(w.buffers):
@@ -36,7 +40,7 @@ def _caller_buffers(w, inputs):
             ptrs.append(0)
             pitch.append(0)
             continue
-        ld = (b.cols + 15) // 16 * 16
+        ld = (b.cols + 15) // 16 * 16 + extra
         t = torch.zeros((b.rows, ld), dtype=torch.float32 if b.dtype == F32 else torch.int16, device="cuda")
         if i in inputs:
             arr = inputs[i] if b.dtype == F32 else inputs[i].view(np.int16)
@@ -56,19 +60,23 @@ def _read(w, tensors, bid):
     return np.ascontiguousarray(a if b.dtype == F32 else a.view(np.uint16))
 
 
+@pytest.mark.parametrize("extra", [0, 48], ids=["pitch_16", "pitch_wide"])
 @pytest.mark.parametrize("make", [
     lambda: fork_join(256, seed=5),
     lambda: encoder_block(batch=2, seq=128, d_model=256, heads=4, d_head=64, ffn=512, seed=13),
 ], ids=["fork_join_f32", "encoder_bf16"])
-def test_no_alloc_matches_the_allocating_path_twice(make):
+def test_no_alloc_matches_the_allocating_path_twice(make, extra):
     import torch
     w = make()
     ins = w.make_inputs()
-    ref = run_gpu(w, ins, resident=True)            # dag_create / dag_submit path
+    # the dag_create / dag_submit path, planned as the no-alloc path plans:
+    # no split K (it needs scratch memory), weights in the caller's layout
+    ref = run_gpu(w, ins, resident=True, opts=options(split_k=1, keep_layout=1))
+    exact = oracle.run(w, ins)
     nodes, _, bufs = describe(w, resident_inputs=True)
     written = written_buffers(w, abi.dag_fusion_host(nodes, [], bufs))
     assert set(written) <= set(ref)
-    tensors, ptrs, pitch = _caller_buffers(w, ins)
+    tensors, ptrs, pitch = _caller_buffers(w, ins, extra)
     stream = torch.cuda.current_stream().cuda_stream
     for call in range(2):
         for bid in written:               # outputs start from garbage each call
@@ -78,11 +86,16 @@ def test_no_alloc_matches_the_allocating_path_twice(make):
         st = abi.dag_run_noalloc(nodes, bufs, ptrs, pitch, None, stream)
         assert st == abi.DAG_OK, abi.last_error()
         for bid in written:
+            got = _read(w, tensors, bid)
+            assert np.array_equal(got.view(np.uint8), ref[bid].view(np.uint8)), (call, bid)
             dt = w.buffers[bid].dtype
-            got = storage_to_f64(_read(w, tensors, bid), dt)
-            want = storage_to_f64(ref[bid], dt)
-            err = oracle.rel_err(got, want)
+            err = oracle.rel_err(storage_to_f64(got, dt), storage_to_f64(oracle.view(w, exact, bid), dt))
             assert err <= node_tolerance(w, bid), (call, bid, err)
+        # the pitch padding of every caller buffer is left as the caller wrote it
+        for root, t in tensors.items():
+            if extra and root in {b if w.buffers[b].view_of < 0 else w.buffers[b].view_of for b in written}:
+                pad = t[:, w.buffers[root].cols + (-w.buffers[root].cols) % 16:]
+                assert bool((pad == -1).all()), (call, root)
 
 
 def test_no_alloc_rejects_a_plan_larger_than_its_fixed_area():
