@@ -158,9 +158,13 @@ typedef enum { DAG_FUSE_NONE = 0, DAG_FUSE_ACT = 1, DAG_FUSE_ALL = 2 } dag_fuse;
  * with the 3 x TF32 split (each operand x = hi + lo, hi = tf32(x),
  * lo = tf32(x - hi); A.B ~= Ahi.Bhi + Ahi.Blo + Alo.Bhi with f32
  * accumulation; about 2^-21 relative error per product), for every f32 GEMM
- * whose operand views start on 16-byte boundaries; the others, and every f32
- * GEMM under DAG_F32_GEMM_SIMT, run as f32 FFMA on the SM cores. */
-typedef enum { DAG_F32_GEMM_TENSOR = 0, DAG_F32_GEMM_SIMT = 1 } dag_f32_gemm;
+ * whose operand views start on 16-byte boundaries: 128 x 128 or 128 x 256
+ * tiles when B is read K-major (trans_b, or a weight kept transposed) and N
+ * exceeds 64, else 128 x 64 tiles; the others, and every f32 GEMM under
+ * DAG_F32_GEMM_SIMT, run as f32 FFMA on the SM cores.
+ * DAG_F32_GEMM_TENSOR_NARROW keeps every tensor-core f32 GEMM on 128 x 64
+ * tiles (for comparisons). */
+typedef enum { DAG_F32_GEMM_TENSOR = 0, DAG_F32_GEMM_SIMT = 1, DAG_F32_GEMM_TENSOR_NARROW = 2 } dag_f32_gemm;
 
 typedef struct dag_handle dag_handle;
 

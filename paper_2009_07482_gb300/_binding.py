@@ -26,7 +26,7 @@ DAG_OP_GEMM, DAG_OP_ADD, DAG_OP_SOFTMAX, DAG_OP_UNARY = 0, 1, 2, 3
 DAG_ACT_NONE, DAG_ACT_RELU, DAG_ACT_GELU = 0, 1, 2
 DAG_BUF_INPUT, DAG_BUF_OUTPUT, DAG_BUF_RESIDENT = 1, 2, 4
 DAG_SCHED_RANK_MODEL, DAG_SCHED_RANK_GIVEN, DAG_SCHED_FIFO = 0, 1, 2
-DAG_F32_GEMM_TENSOR, DAG_F32_GEMM_SIMT = 0, 1
+DAG_F32_GEMM_TENSOR, DAG_F32_GEMM_SIMT, DAG_F32_GEMM_TENSOR_NARROW = 0, 1, 2
 DAG_FUSE_NONE, DAG_FUSE_ACT, DAG_FUSE_ALL = 0, 1, 2
 DAG_TC_GIVEN, DAG_TC_WHOLE, DAG_TC_PER_KERNEL = 0, 1, 2
 

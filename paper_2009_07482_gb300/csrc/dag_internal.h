@@ -18,7 +18,8 @@ enum TileOp : int32_t {
   T_ADD = 2,        // 128-bit elementwise add (+ activation)
   T_UNARY = 3,      // 128-bit elementwise activation
   T_SOFTMAX = 4,    // warp-per-row softmax over whole rows
-  T_GEMM_TF32 = 5   // f32 GEMM on the tensor cores, 3 x TF32 split, 128 x 64
+  T_GEMM_TF32 = 5,  // f32 GEMM on the tensor cores, 3 x TF32 split, 128 x 64
+  T_GEMM_TF32W = 6  // the same, 128 x BN (BN = cfg: 128 or 256), B K-major, K blocks of 16
 };
 
 // f32 SIMT GEMM tile shapes (cfg field of a T_GEMM_F32 tile)
@@ -35,7 +36,9 @@ constexpr int kBM = 128;            // bf16 GEMM tile rows (MMA M)
 constexpr int kBK = 64;             // bf16 K per stage (one 128-byte swizzle row)
 constexpr int kStages = 4;          // TMA -> MMA pipeline depth
 constexpr int kBKF = 32;            // f32 K per stage (one 128-byte swizzle row)
-constexpr int kTf32BN = 64;         // f32 tensor-core tile width
+constexpr int kTf32BN = 64;         // f32 tensor-core tile width (128 x 64 form)
+constexpr int kBKW = 16;            // f32 K per stage of the wide form (64-byte swizzle rows)
+constexpr int kWideP = 8;           // stages per TMEM partial sum of the wide form (128 of K)
 constexpr int kParts = 4;           // TMEM partial slots of an f32 tensor-core tile (4 x 64 columns)
 constexpr int kMaxBN = 256;
 constexpr int kStageA = kBM * kBK * 2;        // 16 KiB

@@ -373,6 +373,7 @@ struct Plan {
   int n_sm = 148, grid = 148;
   std::vector<int> cfg;                 // per node tile config
   std::vector<char> tf32;               // per node: f32 GEMM on the tensor cores (3 x TF32)
+  std::vector<char> tf32w;              // per node: ... in the wide form (128 x 128 / 256, B K-major)
   std::vector<int> nsplit;              // per node: split-K factor S (0 = none)
   std::vector<char> store_t;            // per buffer: a weight kept transposed on the device (layout.cu)
   std::vector<int> t_batch, t_K, t_N;   // its per-batch shape as given (K x N)
@@ -420,6 +421,8 @@ static double tile_time_us(const Plan &P, int v, const TileDesc &t) {
     } else if (t.op == T_GEMM_TF32) {
       // three tf32 MMAs (half the bf16 rate) per product, 128 x 64 tiles
       rate = g_bf16_tflops * 1e12 / P.n_sm / 6.0 * 0.5;
+    } else if (t.op == T_GEMM_TF32W) {
+      rate = g_bf16_tflops * 1e12 / P.n_sm / 6.0 * (t.cfg >= 256 ? 0.8 : 0.65);
     } else {
       rate = g_f32_tflops * 1e12 / P.n_sm * 0.6;
     }
@@ -447,13 +450,19 @@ static void choose_configs(Plan &P) {
   for (int v = 0; v < nn; ++v) maxd = std::max(maxd, depth[v]);
   P.cfg.assign(nn, 0);
   P.tf32.assign(nn, 0);
+  P.tf32w.assign(nn, 0);
   for (int v = 0; v < nn; ++v) {
     const dag_node_desc &n = g.nodes[v];
     if (n.op != DAG_OP_GEMM || g.bufs[n.a].dtype != DAG_F32 || P.opt.f32_gemm == DAG_F32_GEMM_SIMT) continue;
     // TMA operands: 16-byte aligned column views (roots and row pitches are)
     P.tf32[v] = ((size_t)g.coff[n.a] * 4) % 16 == 0 && ((size_t)g.coff[n.b] * 4) % 16 == 0;
+    // the wide form reads B K-major (given so, or a weight kept transposed)
+    // and pays off from 128 output columns on
+    const bool kmajor = n.trans_b || P.store_t[g.root[n.b]];
+    P.tf32w[v] = P.tf32[v] && kmajor && g.N[v] > kTf32BN && P.opt.f32_gemm != DAG_F32_GEMM_TENSOR_NARROW;
   }
   static const int bns[3] = {256, 128, 64};
+  static const int wbns[3] = {256, 128, 128};
   static const int f32c[3][3] = {{F32_128x128, 128, 128}, {F32_128x64, 128, 64}, {F32_64x64, 64, 64}};
   for (int pass = 0; pass < 3; ++pass) {
     // concurrency of a depth level at option index `pass`
@@ -461,7 +470,8 @@ static void choose_configs(Plan &P) {
     for (int v = 0; v < nn; ++v) {
       const dag_node_desc &n = g.nodes[v];
       if (n.op != DAG_OP_GEMM) { level[depth[v]] += 8; continue; }
-      if (P.tf32[v]) level[depth[v]] += ntiles_gemm(g, v, 128, kTf32BN);
+      if (P.tf32w[v]) level[depth[v]] += ntiles_gemm(g, v, 128, wbns[pass]);
+      else if (P.tf32[v]) level[depth[v]] += ntiles_gemm(g, v, 128, kTf32BN);
       else if (g.bufs[n.a].dtype == DAG_BF16) level[depth[v]] += ntiles_gemm(g, v, 128, bns[pass]);
       else level[depth[v]] += ntiles_gemm(g, v, f32c[pass][1], f32c[pass][2]);
     }
@@ -470,7 +480,11 @@ static void choose_configs(Plan &P) {
       if (n.op != DAG_OP_GEMM || P.cfg[v]) continue;
       const bool enough = level[depth[v]] >= P.n_sm * 3 / 4 || pass == 2;
       if (!enough) continue;
-      if (P.tf32[v]) {
+      if (P.tf32w[v]) {
+        int bn = wbns[pass];
+        while (bn > 128 && bn / 2 >= round_up(g.N[v], 64)) bn /= 2;  // no wider than N
+        P.cfg[v] = bn + 100;
+      } else if (P.tf32[v]) {
         P.cfg[v] = kTf32BN + 100;
       } else if (g.bufs[n.a].dtype == DAG_BF16) {
         int bn = bns[pass];
@@ -596,16 +610,28 @@ static void choose_split(Plan &P) {
       if (P.absorbed_by[v] < 0) level[depth[v]] += 8;
       continue;
     }
-    const int bn = g.bufs[n.a].dtype == DAG_BF16 ? P.cfg[v] : 64;
+    const int bn = g.bufs[n.a].dtype == DAG_BF16 || P.tf32w[v] ? P.cfg[v] : 64;
     level[depth[v]] += ntiles_gemm(g, v, 128, std::max(bn, 64));
   }
   for (int v = 0; v < nn; ++v) {
     const dag_node_desc &n = g.nodes[v];
-    if (n.op != DAG_OP_GEMM || g.bufs[n.a].dtype != DAG_BF16) continue;
+    if (n.op != DAG_OP_GEMM) continue;
     const long lt = level[depth[v]];
-    const int kit = (g.K[v] + kBK - 1) / kBK;
-    if (lt * 2 > P.n_sm || kit < 32) continue;
-    const int S = std::min({4, (int)(P.n_sm / std::max(1L, lt)), kit / 16});
+    int S = 0, kit = 0;
+    if (g.bufs[n.a].dtype == DAG_BF16) {
+      kit = (g.K[v] + kBK - 1) / kBK;
+      if (lt * 2 > P.n_sm || kit < 32) continue;
+      S = std::min({4, (int)(P.n_sm / std::max(1L, lt)), kit / 16});
+    } else if (P.tf32w[v]) {
+      // the wide f32 form: at least 4 stages (64 of K) per partial
+      kit = (g.K[v] + kBKW - 1) / kBKW;
+      if (lt * 2 > P.n_sm || kit < 8) continue;
+      S = std::min({4, (int)(P.n_sm / std::max(1L, lt)), kit / 4});
+    } else {
+      continue;
+    }
+    // every partial gets a non-empty share of the K blocks
+    while (S >= 2 && (long)(S - 1) * ((kit + S - 1) / S) >= kit) --S;
     if (S >= 2) P.nsplit[v] = S;
   }
 }
@@ -643,9 +669,9 @@ static void make_tiles(Plan &P) {
       // computed by its GEMM's tiles
     } else if (n.op == DAG_OP_GEMM) {
       const bool bf = g.bufs[n.a].dtype == DAG_BF16;
-      const int op = bf ? T_GEMM_BF16 : P.tf32[v] ? T_GEMM_TF32 : T_GEMM_F32;
+      const int op = bf ? T_GEMM_BF16 : P.tf32w[v] ? T_GEMM_TF32W : P.tf32[v] ? T_GEMM_TF32 : T_GEMM_F32;
       int bm, bn;
-      if (bf) { bm = kBM; bn = P.cfg[v]; }
+      if (bf || P.tf32w[v]) { bm = kBM; bn = P.cfg[v]; }
       else if (P.tf32[v]) { bm = kBM; bn = kTf32BN; }
       else {
         bm = P.cfg[v] == F32_64x64 ? 64 : 128;
@@ -971,8 +997,8 @@ static void roofline(Plan &P) {
 }
 
 static void plan_tiles(Plan &P) {
+  choose_layouts(P);  // first: the f32 tile form depends on B's layout
   choose_configs(P);
-  choose_layouts(P);
   choose_fusion(P);
   choose_split(P);
   make_tiles(P);
@@ -1085,14 +1111,14 @@ static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 static dag_status encode_map(CUtensorMap *m, const void *base, uint64_t d0, uint64_t d1, uint64_t d2,
                              uint64_t stride1_bytes, uint64_t stride2_bytes, uint32_t b0, uint32_t b1,
-                             int dtype = DAG_BF16) {
+                             int dtype = DAG_BF16, CUtensorMapSwizzle sw = CU_TENSOR_MAP_SWIZZLE_128B) {
   const cuuint64_t dims[3] = {d0, d1, d2};
   const cuuint64_t strides[2] = {stride1_bytes, stride2_bytes};
   const cuuint32_t box[3] = {b0, b1, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = p_encode_tiled(m, dtype == DAG_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                               3, const_cast<void *>(base), dims, strides, box,
-                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(DAG_EUNSUPPORTED, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return DAG_OK;
@@ -1130,10 +1156,18 @@ static dag_status gemm_maps(const Plan &P, int v, NodeParams &q, std::vector<CUt
   const uint32_t bn = dt == DAG_BF16 ? P.cfg[v] : kTf32BN;
   CUtensorMap ma, mb;
   dag_status s;
-  if ((s = encode_map(&ma, q.A, K, M, B, q.lda * es, (uint64_t)M * q.lda * es, kb, kBM, dt))) return s;
-  if (q.trans_b) s = encode_map(&mb, q.B, K, N, B, q.ldb * es, (uint64_t)N * q.ldb * es, kb, bn, dt);
-  else s = encode_map(&mb, q.B, N, K, B, q.ldb * es, (uint64_t)K * q.ldb * es, 128 / es, kb, dt);
-  if (s) return s;
+  if (P.tf32w[v]) {
+    // the wide f32 form: boxes {16 (K), 128} and {16 (K), BN}, 64-byte swizzle, B K-major
+    if (!q.trans_b) return fail(DAG_EUNSUPPORTED, "node %d: wide f32 tiles need B K-major", v);
+    const CUtensorMapSwizzle sw = CU_TENSOR_MAP_SWIZZLE_64B;
+    if ((s = encode_map(&ma, q.A, K, M, B, q.lda * es, (uint64_t)M * q.lda * es, kBKW, kBM, dt, sw))) return s;
+    if ((s = encode_map(&mb, q.B, K, N, B, q.ldb * es, (uint64_t)N * q.ldb * es, kBKW, P.cfg[v], dt, sw))) return s;
+  } else {
+    if ((s = encode_map(&ma, q.A, K, M, B, q.lda * es, (uint64_t)M * q.lda * es, kb, kBM, dt))) return s;
+    if (q.trans_b) s = encode_map(&mb, q.B, K, N, B, q.ldb * es, (uint64_t)N * q.ldb * es, kb, bn, dt);
+    else s = encode_map(&mb, q.B, N, K, B, q.ldb * es, (uint64_t)K * q.ldb * es, 128 / es, kb, dt);
+    if (s) return s;
+  }
   q.tmap_a = (int)maps.size(); maps.push_back(ma);
   q.tmap_b = (int)maps.size(); maps.push_back(mb);
   q.tmap_c = -1;
@@ -1781,6 +1815,7 @@ extern "C" dag_status dag_fusion_host(const dag_node_desc *nodes, int n_nodes, c
   if (opts) P.opt = *opts;
   dag_status s = build_graph(nodes, n_nodes, edges, n_edges, buffers, n_buffers, P.g);
   if (s) return s;
+  choose_layouts(P);
   choose_configs(P);
   choose_fusion(P);
   for (int v = 0; v < P.g.nn; ++v) out[v] = P.absorbed_by[v];

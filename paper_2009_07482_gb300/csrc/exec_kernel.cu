@@ -141,10 +141,11 @@ __device__ __forceinline__ void run_scheduler(const ExecParams &p, uint8_t *smem
     mbar_arrive(&ctl->slot_full[slot.idx]);
     slot.next(kSlots);
     if (t < 0) return;
-    if (td.op == T_GEMM_BF16 || td.op == T_GEMM_TF32) {
+    if (td.op == T_GEMM_BF16 || td.op == T_GEMM_TF32 || td.op == T_GEMM_TF32W) {
       const uint64_t dl = globaltimer() + p.timeout_ns;
-      const bool ok = td.op == T_GEMM_BF16 ? gemm_produce(p, td, p.nodes[td.node], smem, ctl, st, dl)
-                                           : tf32_produce(p, td, p.nodes[td.node], smem, ctl, st, dl);
+      const bool ok = td.op == T_GEMM_BF16   ? gemm_produce(p, td, p.nodes[td.node], smem, ctl, st, dl)
+                      : td.op == T_GEMM_TF32 ? tf32_produce(p, td, p.nodes[td.node], smem, ctl, st, dl)
+                                             : tf32w_produce(p, td, p.nodes[td.node], smem, ctl, st, dl);
       if (!ok) {
         record_error(p, E_PIPE_TIMEOUT, t);
         ctl->fail = 1;
@@ -173,22 +174,36 @@ __device__ __forceinline__ void run_mma(const ExecParams &p, uint8_t *smem, Smem
     slot.next(kSlots);
     if (t < 0) return;
     const TileDesc td = p.tiles[t];
-    if (td.op != T_GEMM_BF16 && td.op != T_GEMM_TF32) continue;
+    if (td.op != T_GEMM_BF16 && td.op != T_GEMM_TF32 && td.op != T_GEMM_TF32W) continue;
+    // a wide f32 tile of 256 columns holds both accumulator buffers
+    const bool both = td.op == T_GEMM_TF32W && td.cfg == 256;
     const uint64_t dl = globaltimer() + p.timeout_ns;
     if (!mbar_wait(&ctl->acc_empty[accb], ph[accb] ^ 1u, dl)) { ctl->fail = 1; return; }
     ph[accb] ^= 1u;
+    if (both) {
+      if (!mbar_wait(&ctl->acc_empty[accb ^ 1u], ph[accb ^ 1u] ^ 1u, dl)) { ctl->fail = 1; return; }
+      ph[accb ^ 1u] ^= 1u;
+    }
     tc_fence_after();
     if (p.trace_on) p.trace[t].stamp[S_MMA0] = globaltimer();
     const uint32_t acc = ctl->tmem_base + accb * kAccCols;
-    const bool ok = td.op == T_GEMM_BF16 ? gemm_mma(td, p.nodes[td.node], smem, ctl, st, acc, dl)
-                                         : tf32_mma(p.nodes[td.node], smem, ctl, st, split_par, pq, acc, dl);
+    bool ok;
+    if (td.op == T_GEMM_BF16) {
+      ok = gemm_mma(td, p.nodes[td.node], smem, ctl, st, acc, dl);
+    } else if (td.op == T_GEMM_TF32) {
+      ok = tf32_mma(p.nodes[td.node], smem, ctl, st, split_par, pq, acc, dl);
+    } else {
+      uint32_t tS, tX;
+      tf32w_cols(td, ctl->tmem_base, accb, tS, tX);
+      ok = tf32w_mma(td, p.nodes[td.node], smem, ctl, st, split_par, pq, tS, tX, dl);
+    }
     if (!ok) {
       ctl->fail = 1;
       return;
     }
-    if (td.op == T_GEMM_BF16) mma_commit(&ctl->acc_full[accb]);  // f32 tiles signal per K block
+    if (td.op == T_GEMM_BF16) mma_commit(&ctl->acc_full[accb]);  // f32 tiles signal per partial
     if (p.trace_on) p.trace[t].stamp[S_MMA1] = globaltimer();
-    accb ^= 1u;
+    if (!both) accb ^= 1u;  // a tile holding both buffers leaves the next tile where it started
   }
 }
 
@@ -272,16 +287,33 @@ __device__ __forceinline__ void run_workers(const ExecParams &p, uint8_t *smem, 
     // other partials' sums) and a tile with fused adds (their other operands);
     // its start ticket is drawn after them
     // (the plain variant keeps the split-only form, so its code is unchanged)
-    const bool late = kFused ? p.mode == 0 && (td.op == T_GEMM_BF16 || td.op == T_GEMM_TF32) && !split_partial(td) &&
-                                   (td.split || np.n_post)
+    const bool late = kFused ? p.mode == 0 &&
+                                   (td.op == T_GEMM_BF16 || td.op == T_GEMM_TF32 || td.op == T_GEMM_TF32W) &&
+                                   !split_partial(td) && (td.split || np.n_post)
                              : td.split && !split_partial(td) && p.mode == 0;
+    const bool both = td.op == T_GEMM_TF32W && td.cfg == 256;  // holds both accumulator buffers
     bool ok = true;
     switch (td.op) {
       case T_GEMM_BF16:
-      case T_GEMM_TF32: {
+      case T_GEMM_TF32:
+      case T_GEMM_TF32W: {
         stage_bias(td, np, ctl);
-        const uint32_t acc = ctl->tmem_base + accb * kAccCols;
-        if (td.op == T_GEMM_TF32) {
+        uint32_t acc = ctl->tmem_base + accb * kAccCols;
+        if (td.op == T_GEMM_TF32W) {
+          uint32_t tX;
+          tf32w_cols(td, ctl->tmem_base, accb, acc, tX);
+          const bool mine = tf32w_worker_loop(td, np, smem, ctl, fs, acc, tX, globaltimer() + p.timeout_ns);
+          if (!mine) ws->ok = 0;  // any warp that timed out fails the tile
+          worker_sync();
+          if (late) {  // split K: the other partials' sums; fused adds: their operands
+            if (wt == 0 && ws->ok) {
+              if (!wait_late(p, td, epoch)) ws->ok = 0;
+              else if (p.trace_on) ws->late_ticket = atomicAdd(&p.ctrl->ticket, 1u);
+            }
+            worker_sync();
+          }
+          if (p.trace_on && wt == 0) p.trace[t].stamp[S_ACC] = globaltimer();
+        } else if (td.op == T_GEMM_TF32) {
           const bool mine = tf32_worker_loop(np, smem, ctl, fs, acc, globaltimer() + p.timeout_ns);
           if (!mine) ws->ok = 0;  // any warp that timed out fails the tile
           worker_sync();
@@ -315,8 +347,8 @@ __device__ __forceinline__ void run_workers(const ExecParams &p, uint8_t *smem, 
         ok = ws->ok != 0;
         if (ok) {
           tc_fence_after();
-          if (kFused && np.n_post) gemm_epilogue<true>(p, td, np, ctl, ctl->tmem_base + accb * kAccCols, smem + kSmemStages);
-          else gemm_epilogue<false>(p, td, np, ctl, ctl->tmem_base + accb * kAccCols, smem + kSmemStages);
+          if (kFused && np.n_post) gemm_epilogue<true>(p, td, np, ctl, acc, smem + kSmemStages);
+          else gemm_epilogue<false>(p, td, np, ctl, acc, smem + kSmemStages);
         }
         tc_fence_before();
         break;
@@ -336,8 +368,9 @@ __device__ __forceinline__ void run_workers(const ExecParams &p, uint8_t *smem, 
     worker_sync();
     if (wt == 0) {
       if (p.trace_on) p.trace[t].stamp[S_SYNC] = globaltimer();
-      const bool tc = td.op == T_GEMM_BF16 || td.op == T_GEMM_TF32;
+      const bool tc = td.op == T_GEMM_BF16 || td.op == T_GEMM_TF32 || td.op == T_GEMM_TF32W;
       if (tc) mbar_arrive(&ctl->acc_empty[accb]);
+      if (both) mbar_arrive(&ctl->acc_empty[accb ^ 1u]);
       if (!ok) {
         record_error(p, tc ? E_PIPE_TIMEOUT : E_BAD_TILE, t);
         ctl->fail = 1;
@@ -347,7 +380,7 @@ __device__ __forceinline__ void run_workers(const ExecParams &p, uint8_t *smem, 
       }
       mbar_arrive(&ctl->slot_empty[slot.idx]);
     }
-    if (td.op == T_GEMM_BF16 || td.op == T_GEMM_TF32) accb ^= 1u;
+    if ((td.op == T_GEMM_BF16 || td.op == T_GEMM_TF32 || td.op == T_GEMM_TF32W) && !both) accb ^= 1u;
     slot.next(kSlots);
   }
 }

@@ -409,6 +409,200 @@ __device__ __forceinline__ bool tf32_worker_loop(const NodeParams &np, uint8_t *
   return ok;
 }
 
+// ---------------------------------------------------------------------------
+// f32 GEMM tile on the tensor cores, wide form: 128 x BN (BN = 128 or 256),
+// B K-major, the same 3 x TF32 split.  A stage holds one K block of 16
+// (64-byte rows, 64-byte swizzle):
+//   A area: Ahi [0, 8K), Alo [8K, 16K)
+//   B area: Bhi [0, BN * 64), Blo [BN * 64, 2 * BN * 64)
+// so the split is elementwise at equal offsets (no layout work), and each
+// stage is 2 K steps x 3 MMAs of 128 x BN x 8.  Per K block the stage's
+// shared-memory traffic (TMA write, split read and write, MMA operand reads)
+// is 6 x (8K + BN * 64) bytes for 2 x 128 x BN x 16 x 3 tf32 flops: four times
+// the work per byte of the 128 x 64 form at BN = 256.
+// The tensor cores' f32 accumulation is not round-to-nearest and its error
+// grows with the number of MMAs summed into one accumulator, so the tile's K
+// loop is cut into partials of kWideP stages (128 of K): partial 0 goes
+// straight into the sum S, every later one into X, which the workers add
+// into S (f32, round to nearest) before the MMA issuer may start the next
+// partial there.  S and X: BN = 128 -> the tile's accumulator buffer (S its
+// columns 0..127, X 128..255); BN = 256 -> S the tile's buffer, X the other
+// one (such a tile holds both accumulator buffers).
+// ---------------------------------------------------------------------------
+constexpr int kWideLag = kStages - 1;  // stages the splitters run ahead of a partial's end
+static_assert(kBM * kBKW * 4 * 2 <= kStageA && 256 * kBKW * 4 * 2 <= kStageB, "wide tf32 stage layout");
+
+// K blocks [kb0, kb1) of a wide f32 tile (a split tile's share of the K loop)
+__device__ __forceinline__ void tf32w_krange(const TileDesc &t, const NodeParams &np, int &kb0, int &kb1) {
+  const int kiters = (np.K + kBKW - 1) / kBKW;
+  if (!t.split) { kb0 = 0; kb1 = kiters; return; }
+  const int S = split_count(t), s = split_index(t);
+  const int per = (kiters + S - 1) / S;
+  kb0 = min(kiters, s * per);
+  kb1 = min(kiters, kb0 + per);
+}
+
+// two TMEM column ranges of a wide tile: the sum S and the partial X
+__device__ __forceinline__ void tf32w_cols(const TileDesc &t, uint32_t tmem_base, uint32_t accb, uint32_t &tS,
+                                           uint32_t &tX) {
+  tS = tmem_base + accb * kAccCols;
+  tX = t.cfg == 256 ? tmem_base + (accb ^ 1u) * kAccCols : tS + 128u;
+}
+
+__device__ __forceinline__ bool tf32w_produce(const ExecParams &p, const TileDesc &t, const NodeParams &np,
+                                              uint8_t *smem, SmemCtl *ctl, Ring &st, uint64_t deadline) {
+  const int BN = t.cfg, M = np.M;
+  const int bt = t.r0 / M, m0 = t.r0 - bt * M, n0 = t.c0;
+  int kb0, kb1;
+  tf32w_krange(t, np, kb0, kb1);
+  const CUtensorMap *ta = p.tmaps + np.tmap_a;
+  const CUtensorMap *tb = p.tmaps + np.tmap_b;
+  const uint32_t bytes = (uint32_t)((kBM + BN) * kBKW * 4);
+  uint8_t *sA = smem;
+  uint8_t *sB = smem + kStages * kStageA;
+  for (int kb = kb0; kb < kb1; ++kb) {
+    if (!mbar_wait(&ctl->empty[st.idx], st.phase ^ 1u, deadline)) return false;
+    uint64_t *bar = &ctl->full[st.idx];
+    mbar_arrive_expect_tx(bar, bytes);
+    tma_load_3d(sA + st.idx * kStageA, ta, bar, kb * kBKW, m0, bt);   // box {16 (K), 128 (M)}
+    tma_load_3d(sB + st.idx * kStageB, tb, bar, kb * kBKW, n0, bt);   // box {16 (K), BN (N)}
+    stage_issued(ctl, st.idx);
+    st.next(kStages);
+  }
+  return true;
+}
+
+// MMA side of a wide f32 tile.  Partial q of the CTA's stream of f32
+// partials (shared with the 128 x 64 form) signals pfull[q % kParts]; the
+// workers arrive on pempty[q % kParts] once it is added up.
+__device__ __forceinline__ bool tf32w_mma(const TileDesc &t, const NodeParams &np, uint8_t *smem, SmemCtl *ctl,
+                                          Ring &st, uint32_t &split_par, uint32_t &pq, uint32_t tS, uint32_t tX,
+                                          uint64_t deadline) {
+  const int BN = t.cfg;
+  int kb0, kb1;
+  tf32w_krange(t, np, kb0, kb1);
+  const uint32_t idesc = idesc_tf32((uint32_t)BN);
+  const uint32_t blo_off = (uint32_t)BN * kBKW * 4;
+  uint8_t *sA = smem;
+  uint8_t *sB = smem + kStages * kStageA;
+  uint32_t dst = tS;
+  for (int kb = kb0; kb < kb1; ++kb) {
+    const int j = kb - kb0;
+    if (j % kWideP == 0) {  // a new partial
+      const int part = j / kWideP;
+      const uint32_t ps = pq % kParts;
+      // its barrier slot is free once partial pq - kParts was added up
+      if (!mbar_wait(&ctl->pempty[ps], ((pq / kParts) & 1u) ^ 1u, deadline)) return false;
+      if (part >= 2) {  // X holds partial pq - 1 until the workers have added it into S
+        const uint32_t q1 = pq - 1u;
+        if (!mbar_wait(&ctl->pempty[q1 % kParts], (q1 / kParts) & 1u, deadline)) return false;
+      }
+      dst = part == 0 ? tS : tX;
+    }
+    if (!mbar_wait(&ctl->split[st.idx], (split_par >> st.idx) & 1u, deadline)) return false;
+    split_par ^= 1u << st.idx;
+    tc_fence_after();
+    const uint32_t ahi = smem_u32(sA + st.idx * kStageA), alo = ahi + kBM * kBKW * 4;
+    const uint32_t bhi = smem_u32(sB + st.idx * kStageB), blo = bhi + blo_off;
+#pragma unroll
+    for (int kk = 0; kk < kBKW / 8; ++kk) {
+      const uint64_t dah = smem_desc_sw64(ahi + kk * 32), dal = smem_desc_sw64(alo + kk * 32);
+      const uint64_t dbh = smem_desc_sw64(bhi + kk * 32), dbl = smem_desc_sw64(blo + kk * 32);
+      // the small products first, then the large one
+      mma_tf32(dst, dal, dbh, idesc, (j % kWideP != 0 || kk != 0) ? 1u : 0u);
+      mma_tf32(dst, dah, dbl, idesc, 1u);
+      mma_tf32(dst, dah, dbh, idesc, 1u);
+    }
+    mma_commit(&ctl->empty[st.idx]);
+    if ((j + 1) % kWideP == 0 || kb + 1 == kb1) {
+      mma_commit(&ctl->pfull[pq % kParts]);
+      ++pq;
+    }
+    st.next(kStages);
+  }
+  return true;
+}
+
+// Worker side of a wide f32 tile: each worker warp splits its eighth of every
+// stage (Ahi -> Alo, Bhi -> Blo at equal offsets) and arrives on split[s];
+// kWideLag stages after a partial's last stage it waits for the partial and,
+// from the second on, adds X into S over its lane quadrant and half of the
+// columns.  false if a wait ran out.
+__device__ __forceinline__ bool tf32w_worker_loop(const TileDesc &t, const NodeParams &np, uint8_t *smem,
+                                                  SmemCtl *ctl, Tf32State &fs, uint32_t tS, uint32_t tX,
+                                                  uint64_t deadline) {
+  const int wid = (threadIdx.x - kWorkerBase) >> 5, lane = threadIdx.x & 31;
+  const int BN = t.cfg;
+  const int half = wid >> 2;
+  const uint32_t lanes = (uint32_t)((threadIdx.x >> 5 & 3) * 32) << 16;
+  int kb0, kb1;
+  tf32w_krange(t, np, kb0, kb1);
+  const int n = kb1 - kb0;
+  uint8_t *sA = smem;
+  uint8_t *sB = smem + kStages * kStageA;
+  const int a_chunks = kBM * kBKW * 4 / 16 / 8;   // 64 16-byte chunks of Ahi per warp
+  const int b_chunks = BN * kBKW * 4 / 16 / 8;    // 64 or 128 of Bhi
+  bool ok = true;
+  int part = 0;
+  for (int j = 0; j < n + kWideLag; ++j) {
+    if (j < n) {
+      if (ok) {
+        int w = 0;
+        if (lane == 0) w = stage_wait_use(ctl, fs.st.idx, fs.pass, deadline) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, w, 0) != 0;
+      }
+      if (ok) {
+        uint4 *A4 = reinterpret_cast<uint4 *>(sA + fs.st.idx * kStageA) + wid * a_chunks;
+        uint4 *B4 = reinterpret_cast<uint4 *>(sB + fs.st.idx * kStageB) + wid * b_chunks;
+        uint4 xa[2], xb[4];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) xa[u] = A4[lane + 32 * u];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (u < b_chunks / 32) xb[u] = B4[lane + 32 * u];
+        uint4 *Alo = A4 + kBM * kBKW * 4 / 16;        // Alo sits 8 KiB after Ahi
+        uint4 *Blo = B4 + BN * kBKW * 4 / 16;         // Blo sits BN * 64 bytes after Bhi
+#pragma unroll
+        for (int u = 0; u < 2; ++u) Alo[lane + 32 * u] = tf32_lo4(xa[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (u < b_chunks / 32) Blo[lane + 32 * u] = tf32_lo4(xb[u]);
+        fence_proxy_async_shared();  // generic writes -> visible to the tensor cores
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ctl->split[fs.st.idx]);
+      }
+      fs.st.next(kStages);
+      if (fs.st.idx == 0) ++fs.pass;
+    }
+    const int e = j - kWideLag;  // a stage whose partial may end there
+    if (e >= 0 && (e + 1 == n || (e + 1) % kWideP == 0)) {
+      const uint32_t ps = fs.pq % kParts;
+      if (ok) {
+        int w = 0;
+        if (lane == 0) w = mbar_wait(&ctl->pfull[ps], (fs.pq / kParts) & 1u, deadline) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, w, 0) != 0;
+      }
+      if (ok && part > 0) {
+        tc_fence_after();
+        for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 32) {
+          float x[32], y[32];
+          tmem_ld32x2(tX + lanes + (uint32_t)c, x, tS + lanes + (uint32_t)c, y);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) y[i] += x[i];
+          tmem_st32(tS + lanes + (uint32_t)c, y);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ctl->pempty[ps]);
+      ++fs.pq;
+      ++part;
+    }
+  }
+  if (ok) tc_fence_after();
+  return ok;
+}
+
 // Elementwise kernels fused into a GEMM epilogue, on 32 consecutive values of
 // one output row (row grow, columns col..col+31): each step first rounds the
 // value to the dtype of the buffer the previous kernel would have stored,

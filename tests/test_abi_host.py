@@ -197,21 +197,28 @@ def _f32_gemm_with_views(a_off):
     return w
 
 
-@pytest.mark.parametrize("a_off,mode", [(0, 0), (4, 0), (1, 0), (0, 1)])
+@pytest.mark.parametrize("a_off,mode", [(0, 0), (4, 0), (1, 0), (0, 1), (0, 2)])
 def test_f32_gemm_tile_kind(a_off, mode):
-    """f32 GEMMs take the tensor-core 3 x TF32 tiles (128 x 64) unless an
-    operand view does not start on a 16-byte boundary or SIMT is asked for;
-    then the SIMT FFMA shapes (64/128 rows x 64/128 columns)."""
+    """f32 GEMMs take the tensor-core 3 x TF32 tiles unless an operand view
+    does not start on a 16-byte boundary or SIMT is asked for; then the SIMT
+    FFMA shapes (64/128 rows x 64/128 columns).  With B read K-major (here:
+    resident weights kept transposed) and N > 64 the tiles are 128 x 128 or
+    128 x 256 (the wide form), else -- and always under
+    DAG_F32_GEMM_TENSOR_NARROW -- 128 x 64."""
     w = _f32_gemm_with_views(a_off)
     n, e, b = dagmod.describe(w, resident_inputs=True)
     t, _ = abi.dag_plan_host(n, e, b, dagmod.options(f32_gemm=mode), 148)
-    for node, want_tc in ((0, mode == 0 and a_off % 4 == 0), (1, mode == 0)):
+    for node, want_tc in ((0, mode != 1 and a_off % 4 == 0), (1, mode != 1)):
         mine = t[t[:, 0] == node]
         rows = mine[:, 2] - mine[:, 1]
         cols = mine[:, 4] - mine[:, 3]
-        if want_tc:
+        if want_tc and mode == 2:
             assert (mine[:, 5] == 64).all()
             assert rows.max() == 128 and cols.max() == 64
+        elif want_tc:
+            bn = int(mine[0, 5])
+            assert bn in (128, 256) and ((mine[:, 5] & 0xFFFF) == bn).all()
+            assert rows.max() == 128 and cols.max() <= bn
         else:
             assert set(mine[:, 5].tolist()) <= {0, 1, 2}
 

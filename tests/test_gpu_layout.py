@@ -37,16 +37,28 @@ def _run(w, ins, **opt):
 
 
 def _check(w, transposed):
+    """Weights kept K-major: oracle parity; and the same bits as the caller's
+    layout under one tile form.  f32 GEMMs with a K-major B take the wide
+    128 x 128 / 256 tiles by default, whose partial sums are cut differently
+    from the 128 x 64 tiles an MN-major B gets, so for the bit comparison
+    both runs use the 128 x 64 form (DAG_F32_GEMM_TENSOR_NARROW)."""
     ins = w.make_inputs()
+    ref = oracle.run(w, ins)
     d, got = _run(w, ins)
-    compare(w, got, oracle.run(w, ins))
+    compare(w, got, ref)
     for b, want in transposed.items():
         assert (abi.dag_device_ptr(d.h, b)[0] is None) == want, b
     # every input reads back in the caller's layout
     for b in w.input_ids():
         assert np.array_equal(d.output(b).view(np.uint8), np.ascontiguousarray(ins[b]).view(np.uint8)), b
     d.close()
-    u, base = _run(w, ins, keep_layout=1)
+    f32 = any(w.buffers[n.a].dtype == F32 for n in w.nodes if n.op == "gemm")
+    form = {"f32_gemm": abi.DAG_F32_GEMM_TENSOR_NARROW} if f32 else {}
+    if f32:
+        n, got = _run(w, ins, **form)
+        compare(w, got, ref)
+        n.close()
+    u, base = _run(w, ins, keep_layout=1, **form)
     for b in transposed:
         assert abi.dag_device_ptr(u.h, b)[0] is not None
     u.close()
