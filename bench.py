@@ -82,16 +82,18 @@ def run_timeline(args, w, d, abi, stream, flush, reps=8):
     the launch's first claim) and the median time of each phase of its tiles
     (between consecutive stamps the tile kind records)."""
     import numpy as np
-    windows, phases, spans = {}, {}, []
+    windows, phases, spans, lw = {}, {}, [], []
     for _ in range(reps):
         flush.zero_()
         d.submit(stream.cuda_stream)
         abi.check(d.wait(), "wait")
         recs = d.trace()
         st = abi.dag_trace_stamps(d.h).astype(np.int64)
+        enter, leave = abi.dag_trace_launch(d.h)
         node = np.array([r.node for r in recs])
         t0 = st[:, 0].min()
         spans.append((st[:, 9].max() - t0) / 1e3)
+        lw.append(((t0 - enter) / 1e3, (leave - st[:, 9].max()) / 1e3, (leave - enter) / 1e3))
         for v in range(len(w.nodes)):
             S = st[node == v]
             if not len(S):
@@ -110,7 +112,12 @@ def run_timeline(args, w, d, abi, stream, flush, reps=8):
                     "tiles": int(win[3]), "first_claim_us": round(float(win[0]), 2),
                     "first_ready_us": round(float(win[1]), 2), "last_release_us": round(float(win[2]), 2),
                     "phase_median_us": {k: round(float(np.median(x)), 2) for k, x in phases[v].items()}})
-    return {"traced_launch_us_median": round(float(np.median(spans)), 2), "kernels": out}
+    lw = np.array(lw)
+    return {"traced_launch_us_median": round(float(np.median(spans)), 2),
+            "launch_window_us_median": {"entry_to_first_claim": round(float(np.median(lw[:, 0])), 2),
+                                        "last_release_to_exit": round(float(np.median(lw[:, 1])), 2),
+                                        "entry_to_exit": round(float(np.median(lw[:, 2])), 2)},
+            "kernels": out}
 
 
 def make_workload(name):

@@ -124,7 +124,9 @@ typedef struct {
   int32_t trace;              /* record a per-tile trace (tickets, times, SM) */
   int32_t max_ctas;           /* persistent grid size; 0 = one CTA per SM */
   int32_t scheduler;          /* dag_sched */
-  int32_t tile_override;      /* 0 = automatic; else forces every bf16 GEMM to BN = tile_override (64/128/256) */
+  int32_t tile_override;      /* 0 = automatic; else forces every bf16 GEMM to BN = tile_override (64/128/256),
+                                 and every f32 GEMM that can take the wide tensor-core form to that width
+                                 (128/256; 64 = the 128 x 64 form) */
   const float *node_cost_us;  /* per-node time estimates for DAG_SCHED_RANK_GIVEN (n_nodes entries) */
   int32_t debug_never_ready;  /* test hook: >0 makes that many tiles wait on a counter nothing releases,
                                  so the device wait runs out and reports DAG_ETIMEOUT */
@@ -160,11 +162,19 @@ typedef enum { DAG_FUSE_NONE = 0, DAG_FUSE_ACT = 1, DAG_FUSE_ALL = 2 } dag_fuse;
  * accumulation; about 2^-21 relative error per product), for every f32 GEMM
  * whose operand views start on 16-byte boundaries: 128 x 128 or 128 x 256
  * tiles when B is read K-major (trans_b, or a weight kept transposed) and N
- * exceeds 64, else 128 x 64 tiles; the others, and every f32 GEMM under
+ * exceeds 64 -- except in a DAG level too small for 128-column tiles with a
+ * K loop too short to split (K < 1024), where twice as many 128 x 64 tiles
+ * fill more SMs -- else 128 x 64 tiles; the others, and every f32 GEMM under
  * DAG_F32_GEMM_SIMT, run as f32 FFMA on the SM cores.
  * DAG_F32_GEMM_TENSOR_NARROW keeps every tensor-core f32 GEMM on 128 x 64
+ * tiles, DAG_F32_GEMM_TENSOR_WIDE puts every one that can on 128 x 128 / 256
  * tiles (for comparisons). */
-typedef enum { DAG_F32_GEMM_TENSOR = 0, DAG_F32_GEMM_SIMT = 1, DAG_F32_GEMM_TENSOR_NARROW = 2 } dag_f32_gemm;
+typedef enum {
+  DAG_F32_GEMM_TENSOR = 0,
+  DAG_F32_GEMM_SIMT = 1,
+  DAG_F32_GEMM_TENSOR_NARROW = 2,
+  DAG_F32_GEMM_TENSOR_WIDE = 3
+} dag_f32_gemm;
 
 typedef struct dag_handle dag_handle;
 
@@ -521,6 +531,14 @@ dag_status dag_trace_get(dag_handle *h, dag_trace_record *out, int cap, int *n);
  * stores issued, fence and barrier done, release done (0 where a phase does
  * not apply).  out holds 10 * cap values.  Diagnostic; needs opts.trace. */
 dag_status dag_trace_stamps(dag_handle *h, uint64_t *out, int cap, int *n);
+
+/* dag_trace_launch: the window of the last persistent launch traced (needs
+ * dag_options.trace): enter_exit[0] = the earliest CTA entry, enter_exit[1] =
+ * the latest CTA exit, on the %globaltimer clock (ns) of dag_trace_stamps, so
+ * that the executor's own start-up and tear-down show beside the tiles' phases
+ * (the launch's part of the paper's Gantt charts, §2 and §6).  DAG_EINVAL if
+ * tracing is off or the last submit was not a persistent launch. */
+dag_status dag_trace_launch(dag_handle *h, uint64_t *enter_exit);
 
 /* Static plan facts. */
 typedef struct {

@@ -26,7 +26,7 @@ DAG_OP_GEMM, DAG_OP_ADD, DAG_OP_SOFTMAX, DAG_OP_UNARY = 0, 1, 2, 3
 DAG_ACT_NONE, DAG_ACT_RELU, DAG_ACT_GELU = 0, 1, 2
 DAG_BUF_INPUT, DAG_BUF_OUTPUT, DAG_BUF_RESIDENT = 1, 2, 4
 DAG_SCHED_RANK_MODEL, DAG_SCHED_RANK_GIVEN, DAG_SCHED_FIFO = 0, 1, 2
-DAG_F32_GEMM_TENSOR, DAG_F32_GEMM_SIMT, DAG_F32_GEMM_TENSOR_NARROW = 0, 1, 2
+DAG_F32_GEMM_TENSOR, DAG_F32_GEMM_SIMT, DAG_F32_GEMM_TENSOR_NARROW, DAG_F32_GEMM_TENSOR_WIDE = 0, 1, 2, 3
 DAG_FUSE_NONE, DAG_FUSE_ACT, DAG_FUSE_ALL = 0, 1, 2
 DAG_TC_GIVEN, DAG_TC_WHOLE, DAG_TC_PER_KERNEL = 0, 1, 2
 
@@ -142,6 +142,7 @@ _SIGS = {
     "dag_set_peaks": (None, [C.c_double, C.c_double, C.c_double]),
     "dag_set_device": (i32, [C.c_int]),
     "dag_trace_stamps": (i32, [C.c_void_p, C.POINTER(u64), C.c_int, C.POINTER(C.c_int)]),
+    "dag_trace_launch": (i32, [C.c_void_p, C.POINTER(u64)]),
     "dag_node_costs_get": (i32, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "dag_poll": (i32, [C.c_void_p]),
     "dag_server_create": (i32, [C.POINTER(dag_model_desc), C.c_int, C.c_int, C.c_size_t, C.POINTER(dag_options),
@@ -365,6 +366,13 @@ def dag_run_noalloc(nodes, buffers, buffer_ptrs, row_pitch, options: Optional[da
     la = (C.c_int64 * max(1, nb))(*row_pitch)
     return int(lib().dag_run_noalloc(na, nn, ba, nb, pa, la, C.byref(options) if options else None,
                                      C.c_void_p(stream)))
+
+
+def dag_trace_launch(h):
+    """(first CTA entry, last CTA exit) of the last traced persistent launch, ns."""
+    out = (u64 * 2)()
+    check(lib().dag_trace_launch(h, out), "dag_trace_launch")
+    return int(out[0]), int(out[1])
 
 
 def dag_plan_get(h) -> dag_plan_info:

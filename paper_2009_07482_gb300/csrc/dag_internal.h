@@ -120,6 +120,8 @@ struct Ctrl {
   uint32_t err_tile;
   uint32_t abort;       // set on error: every CTA leaves its waits
   uint32_t pad;
+  uint64_t t_enter;     // tracing: earliest CTA entry of the launch (%globaltimer ns)
+  uint64_t t_exit;      // tracing: latest CTA exit
 };
 
 enum DevErr : uint32_t { E_NONE = 0, E_DEP_TIMEOUT = 1, E_PIPE_TIMEOUT = 2, E_BAD_TILE = 3 };

@@ -480,7 +480,12 @@ static void choose_configs(Plan &P) {
       if (n.op != DAG_OP_GEMM || P.cfg[v]) continue;
       const bool enough = level[depth[v]] >= P.n_sm * 3 / 4 || pass == 2;
       if (!enough) continue;
-      if (P.tf32w[v]) {
+      if (P.tf32w[v] && pass == 2 && g.K[v] < 1024 && P.opt.f32_gemm != DAG_F32_GEMM_TENSOR_WIDE) {
+        // a level too small for 128-column tiles and a short K loop (no
+        // split): twice as many 128 x 64 tiles fill more SMs
+        P.tf32w[v] = 0;
+        P.cfg[v] = kTf32BN + 100;
+      } else if (P.tf32w[v]) {
         int bn = wbns[pass];
         while (bn > 128 && bn / 2 >= round_up(g.N[v], 64)) bn /= 2;  // no wider than N
         P.cfg[v] = bn + 100;
@@ -503,6 +508,16 @@ static void choose_configs(Plan &P) {
         P.cfg[v] = P.opt.tile_override;
     } else {
       P.cfg[v] -= 100;
+      // an f32 GEMM that can take the wide form: 128 / 256 forces that width, 64 the 128 x 64 form
+      const bool can_wide = P.tf32[v] && (n.trans_b || P.store_t[g.root[n.b]]) && g.N[v] > kTf32BN &&
+                            P.opt.f32_gemm != DAG_F32_GEMM_TENSOR_NARROW;
+      if (can_wide && (P.opt.tile_override == 128 || P.opt.tile_override == 256)) {
+        P.tf32w[v] = 1;
+        P.cfg[v] = P.opt.tile_override;
+      } else if (can_wide && P.opt.tile_override == 64) {
+        P.tf32w[v] = 0;
+        P.cfg[v] = kTf32BN;
+      }
     }
   }
 }
@@ -623,10 +638,10 @@ static void choose_split(Plan &P) {
       if (lt * 2 > P.n_sm || kit < 32) continue;
       S = std::min({4, (int)(P.n_sm / std::max(1L, lt)), kit / 16});
     } else if (P.tf32w[v]) {
-      // the wide f32 form: at least 4 stages (64 of K) per partial
+      // the wide f32 form: at least 16 stages (256 of K) per partial
       kit = (g.K[v] + kBKW - 1) / kBKW;
-      if (lt * 2 > P.n_sm || kit < 8) continue;
-      S = std::min({4, (int)(P.n_sm / std::max(1L, lt)), kit / 4});
+      if (lt * 2 > P.n_sm || kit < 32) continue;
+      S = std::min({4, (int)(P.n_sm / std::max(1L, lt)), kit / 16});
     } else {
       continue;
     }
@@ -1538,7 +1553,11 @@ extern "C" dag_status dag_submit(dag_handle *h, void *stream_) {
       return fail(DAG_EDEVICE, "cuStreamWriteValue32");
     }
   }
-  if (P.opt.trace && P.tiles.size()) CUDA_TRY(cudaMemsetAsync(h->d_trace, 0, P.tiles.size() * sizeof(TraceRec), stream));
+  if (P.opt.trace && P.tiles.size()) {
+    CUDA_TRY(cudaMemsetAsync(h->d_trace, 0, P.tiles.size() * sizeof(TraceRec), stream));
+    CUDA_TRY(cudaMemsetAsync(&h->d_ctrl->t_enter, 0xFF, sizeof(uint64_t), stream));  // the launch's window
+    CUDA_TRY(cudaMemsetAsync(&h->d_ctrl->t_exit, 0, sizeof(uint64_t), stream));
+  }
   if (P.tiles.size() && P.opt.use_graph) {
     if (!h->gexec) {  // capture the persistent launch once; replays reuse it
       if (!h->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
@@ -1594,7 +1613,11 @@ extern "C" dag_status dag_submit_coarse(dag_handle *h, void *stream_) {
   }
   ExecParams x = h->xp;
   x.tiles = h->d_coarse;
-  if (P.opt.trace && P.tiles.size()) CUDA_TRY(cudaMemsetAsync(h->d_trace, 0, P.tiles.size() * sizeof(TraceRec), stream));
+  if (P.opt.trace && P.tiles.size()) {
+    CUDA_TRY(cudaMemsetAsync(h->d_trace, 0, P.tiles.size() * sizeof(TraceRec), stream));
+    CUDA_TRY(cudaMemsetAsync(&h->d_ctrl->t_enter, 0xFF, sizeof(uint64_t), stream));  // the launch's window
+    CUDA_TRY(cudaMemsetAsync(&h->d_ctrl->t_exit, 0, sizeof(uint64_t), stream));
+  }
   for (int v : P.g.topo)
     if (launch_in_turn(P, v) >= 0) CUDA_TRY(launch_node_coarse(x, P, launch_in_turn(P, v), stream));
   CUDA_TRY(cudaEventRecord(h->ev_done, stream));
@@ -1740,6 +1763,18 @@ extern "C" dag_status dag_trace_get(dag_handle *h, dag_trace_record *out, int ca
                               t.split, 0, tr[i].stamp[S_CLAIM], tr[i].stamp[S_READY], tr[i].stamp[S_WORK],
                               tr[i].stamp[S_END]};
   }
+  return DAG_OK;
+}
+
+extern "C" dag_status dag_trace_launch(dag_handle *h, uint64_t *enter_exit) {
+  if (!h || !enter_exit) return fail(DAG_EINVAL, "null argument");
+  if (h->in_flight) return fail(DAG_EBUSY, "call dag_wait first");
+  if (!h->P.opt.trace) return fail(DAG_EINVAL, "tracing was not enabled in dag_options");
+  if (h->last_mode != 0) return fail(DAG_EINVAL, "the last submit was not a persistent launch");
+  Ctrl c;
+  CUDA_TRY(cudaMemcpy(&c, h->d_ctrl, sizeof c, cudaMemcpyDeviceToHost));
+  enter_exit[0] = c.t_enter;
+  enter_exit[1] = c.t_exit;
   return DAG_OK;
 }
 

@@ -395,6 +395,7 @@ __global__ void __launch_bounds__(kThreads, 1) dag_exec_kernel(const __grid_cons
   SmemCtl *ctl = reinterpret_cast<SmemCtl *>(smem + kSmemStages + kWorkerScratch);
   __shared__ WorkerShared ws;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0 && p.trace_on) atomicMin(reinterpret_cast<unsigned long long *>(&p.ctrl->t_enter), globaltimer());
 
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -461,6 +462,7 @@ __global__ void __launch_bounds__(kThreads, 1) dag_exec_kernel(const __grid_cons
       atomicAdd(&p.ctrl->epoch, 1u);
     }
   }
+  if (tid == 0 && p.trace_on) atomicMax(reinterpret_cast<unsigned long long *>(&p.ctrl->t_exit), globaltimer());
 }
 
 int exec_smem_bytes() { return kSmemBytes; }

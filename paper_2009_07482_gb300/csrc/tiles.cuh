@@ -1169,6 +1169,95 @@ __device__ __forceinline__ void softmax_rows_vec256(const NodeParams &np, int r0
   }
 }
 
+// Rows of 257..2048 elements (N a multiple of 4, 16-byte aligned rows): lane
+// l holds the 4-element groups l, l + 32, ..., l + 32 (G - 1) of each of R
+// rows in registers -- one read of the input and one write of the output per
+// row, with the loads of the R rows issued before any arithmetic (4 G R
+// values per lane, 64 at most; more rows in flight made the executor kernel
+// spill registers) -- max and sum by interleaved shuffle reductions, __expf
+// as in the 256-element path.
+template <int G, int R, int ADT>
+__device__ __forceinline__ void softmax_rows_wide(const NodeParams &np, int r0, int r1, int stride) {
+  const int lane = threadIdx.x & 31;
+  const int N = np.N;
+  const float s = np.scale;
+  void *const C = np.C;
+  const int c_dt = np.c_dt;
+  const int64_t lda = np.lda, ldc = np.ldc;
+  for (int rb = r0; rb < r1; rb += R * stride) {
+    float v[R][G][4];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int r = rb + q * stride;
+#pragma unroll
+      for (int i = 0; i < G; ++i) {
+        const int j = 4 * (lane + 32 * i);
+        const bool ok = r < r1 && j < N;
+        if (ADT == 0) {
+          const float4 a = ok ? __ldcg(reinterpret_cast<const float4 *>(static_cast<const float *>(np.A) +
+                                                                       (int64_t)r * lda + j))
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+          v[q][i][0] = a.x; v[q][i][1] = a.y; v[q][i][2] = a.z; v[q][i][3] = a.w;
+        } else {
+          const uint2 a = ok ? __ldcg(reinterpret_cast<const uint2 *>(static_cast<const uint16_t *>(np.A) +
+                                                                     (int64_t)r * lda + j))
+                             : make_uint2(0u, 0u);
+          v[q][i][0] = __uint_as_float(a.x << 16); v[q][i][1] = __uint_as_float(a.x & 0xFFFF0000u);
+          v[q][i][2] = __uint_as_float(a.y << 16); v[q][i][3] = __uint_as_float(a.y & 0xFFFF0000u);
+        }
+      }
+    }
+    float m[R], sum[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      m[q] = -INFINITY;
+#pragma unroll
+      for (int i = 0; i < G; ++i) {
+        const bool ok = 4 * (lane + 32 * i) < N;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          v[q][i][e] = s * v[q][i][e];
+          if (ok) m[q] = fmaxf(m[q], v[q][i][e]);
+        }
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+      for (int q = 0; q < R; ++q) m[q] = fmaxf(m[q], __shfl_xor_sync(0xffffffffu, m[q], off));
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      sum[q] = 0.f;
+#pragma unroll
+      for (int i = 0; i < G; ++i) {
+        const bool ok = 4 * (lane + 32 * i) < N;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          v[q][i][e] = ok ? __expf(v[q][i][e] - m[q]) : 0.f;
+          sum[q] += v[q][i][e];
+        }
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+      for (int q = 0; q < R; ++q) sum[q] += __shfl_xor_sync(0xffffffffu, sum[q], off);
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int r = rb + q * stride;
+      if (r >= r1) continue;
+      const float inv = 1.f / sum[q];
+#pragma unroll
+      for (int i = 0; i < G; ++i) {
+        const int j = 4 * (lane + 32 * i);
+        if (j >= N) continue;
+        const float o[4] = {v[q][i][0] * inv, v[q][i][1] * inv, v[q][i][2] * inv, v[q][i][3] * inv};
+        store4(C, c_dt, (int64_t)r * ldc + j, o);
+      }
+    }
+  }
+}
+
 __device__ __noinline__ void tile_softmax(const TileDesc &t, const NodeParams &np) {
   const int wid = (threadIdx.x - kWorkerBase) >> 5, lane = threadIdx.x & 31;
   constexpr int nw = kWorkers / 32;
@@ -1176,6 +1265,17 @@ __device__ __noinline__ void tile_softmax(const TileDesc &t, const NodeParams &n
   if (N <= 256 && np.vec && (N & 3) == 0) {
     if (np.a_dt == 0) softmax_rows_vec256<4, 0>(np, t.r0 + wid, t.r1, nw);
     else softmax_rows_vec256<4, 1>(np, t.r0 + wid, t.r1, nw);
+  } else if (N <= 2048 && np.vec && (N & 3) == 0) {
+    if (N <= 512) {
+      if (np.a_dt == 0) softmax_rows_wide<4, 2, 0>(np, t.r0 + wid, t.r1, nw);
+      else softmax_rows_wide<4, 2, 1>(np, t.r0 + wid, t.r1, nw);
+    } else if (N <= 1024) {
+      if (np.a_dt == 0) softmax_rows_wide<8, 1, 0>(np, t.r0 + wid, t.r1, nw);
+      else softmax_rows_wide<8, 1, 1>(np, t.r0 + wid, t.r1, nw);
+    } else {
+      if (np.a_dt == 0) softmax_rows_wide<16, 1, 0>(np, t.r0 + wid, t.r1, nw);
+      else softmax_rows_wide<16, 1, 1>(np, t.r0 + wid, t.r1, nw);
+    }
   } else if (N <= 256) {
     softmax_rows_reg<8>(np, t.r0 + wid, t.r1, nw);
   } else if (N <= 1024) {

@@ -203,11 +203,16 @@ def test_f32_gemm_tile_kind(a_off, mode):
     does not start on a 16-byte boundary or SIMT is asked for; then the SIMT
     FFMA shapes (64/128 rows x 64/128 columns).  With B read K-major (here:
     resident weights kept transposed) and N > 64 the tiles are 128 x 128 or
-    128 x 256 (the wide form), else -- and always under
+    128 x 256 (the wide form) when the level has tiles enough for the SMs
+    (planned here for a 4-SM GPU), else -- and always under
     DAG_F32_GEMM_TENSOR_NARROW -- 128 x 64."""
     w = _f32_gemm_with_views(a_off)
     n, e, b = dagmod.describe(w, resident_inputs=True)
-    t, _ = abi.dag_plan_host(n, e, b, dagmod.options(f32_gemm=mode), 148)
+    t, _ = abi.dag_plan_host(n, e, b, dagmod.options(f32_gemm=mode), 4)
+    # the same level on a full GPU with a short K loop: twice as many 128 x 64 tiles
+    t_full, _ = abi.dag_plan_host(n, e, b, dagmod.options(f32_gemm=mode), 148)
+    if mode == 0 and a_off % 4 == 0:
+        assert ((t_full[:, 5] & 0xFFFF) == 64).all()
     for node, want_tc in ((0, mode != 1 and a_off % 4 == 0), (1, mode != 1)):
         mine = t[t[:, 0] == node]
         rows = mine[:, 2] - mine[:, 1]

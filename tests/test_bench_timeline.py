@@ -34,13 +34,17 @@ def test_timeline_windows_and_phases():
     e3 = [6600, 7000, 0, 0, 0, 7100, 0, 8100, 8200, 9000]
     stamps = np.array([g0, g1, e3], dtype=np.int64) + base
     stamps[2, [2, 3, 4, 6]] = 0            # phases an elementwise tile does not stamp
+    # the launch: entered 2 us before the first claim, left 1.5 us after the last release
     fake_abi = types.SimpleNamespace(check=lambda st, what: None,
-                                     dag_trace_stamps=lambda h: stamps.astype(np.uint64))
+                                     dag_trace_stamps=lambda h: stamps.astype(np.uint64),
+                                     dag_trace_launch=lambda h: (base - 2000, base + 9000 + 1500))
     flush = types.SimpleNamespace(zero_=lambda: None)
     stream = types.SimpleNamespace(cuda_stream=0)
     d = _FakeDag(stamps, [0, 0, 3])
     out = bench.run_timeline(None, w, d, fake_abi, stream, flush, reps=3)
     assert out["traced_launch_us_median"] == 9.0
+    assert out["launch_window_us_median"] == {"entry_to_first_claim": 2.0, "last_release_to_exit": 1.5,
+                                              "entry_to_exit": 12.5}
     k = {x["kernel"]: x for x in out["kernels"]}
     assert set(k) == {0, 3}
     assert (k[0]["tiles"], k[0]["first_claim_us"], k[0]["first_ready_us"], k[0]["last_release_us"]) == (2, 0.0, 0.5, 6.5)

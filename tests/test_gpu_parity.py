@@ -158,21 +158,23 @@ WIDE_CASES = [
 ]
 
 
+@pytest.mark.parametrize("bn", [128, 256])
 @pytest.mark.parametrize("case", WIDE_CASES, ids=lambda c: "-".join(f"{k}{v}" for k, v in c.items()))
-def test_gemm_f32_wide_tiles(case):
+def test_gemm_f32_wide_tiles(case, bn):
     """The wide 3 x TF32 form (128 x 128 / 128 x 256 tiles, B K-major, K in
     stages of 16, partial sums every 128 of K added up in f32) within the
-    f32 tolerance of the oracle, in both launch forms."""
+    f32 tolerance of the oracle, in both launch forms, whole K per tile."""
     w = _gemm_case(**case)
-    tiles, _ = _resident_roundtrip(w)
-    assert set((tiles[:, 5] & 0xFFFF).tolist()) <= {128, 256}, "not planned as wide f32 tiles"
+    tiles, _ = _resident_roundtrip(w, options(trace=1, tile_override=bn, split_k=1))
+    assert set((tiles[:, 5] & 0xFFFF).tolist()) == {bn}, "not planned as wide f32 tiles of that width"
+    assert not ((tiles[:, 5] >> 16) > 0).any()
 
 
 def test_gemm_f32_wide_and_narrow_agree_with_the_oracle():
     """The same f32 GEMM in the wide and the 128 x 64 form: both within the
     f32 tolerance (their bits differ: the partial sums are cut differently)."""
     w = _gemm_case(M=256, N=384, K=1536, dt=F32, act="relu")
-    t_w, g_w = _resident_roundtrip(w, options(trace=1))
+    t_w, g_w = _resident_roundtrip(w, options(trace=1, f32_gemm=abi.DAG_F32_GEMM_TENSOR_WIDE))
     t_n, g_n = _resident_roundtrip(w, options(trace=1, f32_gemm=abi.DAG_F32_GEMM_TENSOR_NARROW))
     assert set((t_w[:, 5] & 0xFFFF).tolist()) <= {128, 256} and set((t_n[:, 5] & 0xFFFF).tolist()) == {64}
 
@@ -190,10 +192,12 @@ def test_gemm_f32_wide_split_k(case):
     in a fixed order by the finishing tile: within the f32 tolerance, and the
     same bits on every run, grid size and on Alg. 1's streams."""
     w = _gemm_case(**case)
-    tiles, outs = _resident_roundtrip(w)
+    wide = abi.DAG_F32_GEMM_TENSOR_WIDE
+    tiles, outs = _resident_roundtrip(w, options(trace=1, f32_gemm=wide))
     assert ((tiles[:, 5] >> 16) > 0).any(), "not split"
+    assert set((tiles[:, 5] & 0xFFFF).tolist()) <= {128, 256}
     ins = w.make_inputs()
-    for o in (options(max_ctas=3), options(max_ctas=1), options()):
+    for o in (options(max_ctas=3, f32_gemm=wide), options(max_ctas=1, f32_gemm=wide), options(f32_gemm=wide)):
         d = Dag(w, o, resident_inputs=True)
         d.set_inputs(ins)
         d.run()
@@ -279,7 +283,13 @@ def test_gemm_bf16_every_tile_width(bn, trans_b, out_dt):
                                                   # vector path (N a multiple of 4, at most 256): both
                                                   # halves of a lane's elements, one, and partial rows
                                                   (128, BF16, BF16, 1.0), (252, F32, F32, 1.0),
-                                                  (4, F32, BF16, 1.0), (60, BF16, F32, 0.25), (132, F32, F32, 0.5)])
+                                                  (4, F32, BF16, 1.0), (60, BF16, F32, 0.25), (132, F32, F32, 0.5),
+                                                  # rows of 257..2048 held in registers (4 / 8 / 16 groups
+                                                  # of 4 per lane), ragged last groups, and the fallbacks
+                                                  # beyond (N > 2048, N not a multiple of 4)
+                                                  (260, F32, F32, 1.0), (516, BF16, BF16, 0.5), (772, F32, BF16, 1.0),
+                                                  (1500, BF16, F32, 0.125), (2044, F32, F32, 0.25),
+                                                  (2052, F32, F32, 1.0), (1023, BF16, BF16, 1.0)])
 def test_softmax(N, dt_in, dt_out, scale):
     w = Workload("softmax")
     x = w.buf(300, N, dt_in, "input", ("uniform", 5))
