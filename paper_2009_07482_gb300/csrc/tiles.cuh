@@ -574,8 +574,17 @@ __device__ __forceinline__ bool tf32w_worker_loop(const TileDesc &t, const NodeP
       fs.st.next(kStages);
       if (fs.st.idx == 0) ++fs.pass;
     }
-    const int e = j - kWideLag;  // a stage whose partial may end there
-    if (e >= 0 && (e + 1 == n || (e + 1) % kWideP == 0)) {
+    // the next partial to add up ends at stage e_next; it is added up as soon
+    // as the MMA issuer has finished it (checked after every split), and at
+    // the latest kWideLag stages after its end
+    const int e_next = min(n, (part + 1) * kWideP) - 1;
+    bool due = part * kWideP < n && j >= e_next + kWideLag;
+    if (!due && part * kWideP < n && j >= e_next && ok) {
+      int r = 0;
+      if (lane == 0) r = mbar_try_wait(&ctl->pfull[fs.pq % kParts], (fs.pq / kParts) & 1u) ? 1 : 0;
+      due = __shfl_sync(0xffffffffu, r, 0) != 0;
+    }
+    if (due) {
       const uint32_t ps = fs.pq % kParts;
       if (ok) {
         int w = 0;
