@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="batched: skip the cost-model comparison")
     ap.add_argument("--no-configs", action="store_true", help="batched: skip the single-DAG configurations")
+    ap.add_argument("--dags", type=int, default=256,
+                    help="batched: number of DAGs (256 = the configuration; fewer only for profiling captures)")
     ap.add_argument("--profile", action="store_true", help="few steps, no side measurements (for ncu)")
     ap.add_argument("--f32-simt", action="store_true", help="f32 GEMMs on the SM cores (FFMA) instead of 3 x TF32")
     ap.add_argument("--timeline", action="store_true",
@@ -120,14 +122,15 @@ def run_timeline(args, w, d, abi, stream, flush, reps=8):
             "kernels": out}
 
 
-def make_workload(name):
+def make_workload(name, n_dags=256):
     """(workload, description); for "batched" the workload is the list of DAGs."""
     from synth.workloads import branchy_mlp, encoder_block, fork_join, random_batch
     if name == "batched":
         rank = int(os.environ.get("RANK", 0))
-        return random_batch(256, base_seed=1000 + 256 * rank), ("256 seeded random layered DAGs (8-64 nodes, widths 1-8; GEMM 70% / eltwise 20% / "
-                                   "softmax 10%; M,N,K in {64..2048}; bf16 or f32 per DAG) in one persistent launch "
-                                   "replayed from a CUDA graph")
+        return random_batch(n_dags, base_seed=1000 + 256 * rank), (
+            f"{n_dags} seeded random layered DAGs (8-64 nodes, widths 1-8; GEMM 70% / eltwise 20% / "
+            "softmax 10%; M,N,K in {64..2048}; bf16 or f32 per DAG) in one persistent launch "
+            "replayed from a CUDA graph")
     if name == "mlp_bf16":
         return branchy_mlp("bf16"), ("branchy MLP inference DAG, bf16 in / f32 accumulate: batch 512, 4 branches x 3 "
                                      "Linear(2048,2048)+bias+ReLU, add tree, Linear(2048,4096)+ReLU, Linear(4096,1024)")
@@ -407,9 +410,9 @@ def oracle_model(workload, ra=4, rb=12):
     if workload == "batched":
         ws, pick, f_s, f_b = batch_sample()
         t = _batch_sample_seconds(ws, pick)
-        return (t * f_b / f_s / 256,
+        return (t * f_b / f_s,
                 f"random batch: the first {BATCH_ROWS} rows of each of {len(pick)} DAGs (every 8th) in {t:.2f} s; "
-                f"extrapolated to the batch by GEMM flops (x{f_b / f_s:.0f}), per DAG = the batch / 256",
+                f"extrapolated to the 256-DAG batch by GEMM flops (x{f_b / f_s:.0f})",
                 (None, 0, t, 0.0))
     raise ValueError(f"no oracle sample for workload {workload}")
 
@@ -958,7 +961,7 @@ def main():
     peaks, peaks_src = load_peaks()
     abi.dag_set_peaks(peaks["bf16_tflops"], 0.0, peaks["hbm_gbs"])
 
-    wl, desc = make_workload(args.workload)
+    wl, desc = make_workload(args.workload, args.dags)
     batched = isinstance(wl, list)
     from synth.workloads import concat
     w = concat(wl) if batched else wl
