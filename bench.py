@@ -727,12 +727,17 @@ def learned_eval_batched(wl, ins, abi, Dag, options, timed_fn):
     model_tile = model_costs / np.ceil(np.maximum(counts, 1) / grid)
     # learned model trained on traces of other random DAGs, alone and in
     # batches of 2..64 (so its concurrency feature covers batched plans)
-    from synth.workloads import random_batch
+    from synth.workloads import random_batch, random_layered
     trF, trT = [], []
     seed = 5000
     for k in (1, 1, 1, 1, 2, 4, 8, 16, 32, 64):
         rw = concat(random_batch(k, base_seed=seed))
         seed += k
+        F, t, *_ = measure(rw, rw.make_inputs(_INPUTS))
+        trF.append(F)
+        trT.append(t)
+    for i in range(8):  # single DAGs with sizes up to 4096 (beyond the batch's 2048)
+        rw = random_layered(5200 + i, 8, 24, 4, sizes=(64, 128, 256, 512, 1024, 2048, 4096))
         F, t, *_ = measure(rw, rw.make_inputs(_INPUTS))
         trF.append(F)
         trT.append(t)
@@ -742,6 +747,7 @@ def learned_eval_batched(wl, ins, abi, Dag, options, timed_fn):
     Fb = features(wcat, tiles, grid)
     learn_tile = cm.predict_tile_us(Fb)
     learn_costs = node_costs_from_tile_times(learn_tile, counts, grid)
+    chain = chain_and_fill_eval(cm, abi, Dag, options, timed_fn)
     cm.close()
     res = {"mape_learned_vs_profile": mape(learn_tile, prof_tile),
            "mape_roofline_vs_profile": mape(model_tile, prof_tile), "makespan_us": {}}
@@ -757,7 +763,37 @@ def learned_eval_batched(wl, ins, abi, Dag, options, timed_fn):
     ms = res["makespan_us"]
     res["regret_learned_vs_profile"] = ms["rank_learned"] / ms["rank_profile"] - 1.0
     res["gain_learned_vs_roofline_model"] = ms["rank_roofline_model"] / ms["rank_learned"] - 1.0
+    res["chain_and_fill"] = chain
     return res
+
+
+def chain_and_fill_eval(cm, abi, Dag, options, timed_fn, reps=9):
+    """The DAG where the cost source decides the order: a chain of 48 small,
+    latency-bound bf16 GEMMs (the critical path; the roofline model prices each
+    at a fraction of its measured time) beside four 4096^3 GEMMs.  Makespan
+    with the critical-path priority under roofline, measured-profile and
+    learned costs, and FIFO."""
+    from paper_2009_07482_gb300.costmodel import profile_costs
+    from synth.workloads import chain_and_fill
+    w = chain_and_fill()
+    ins = w.make_inputs(_INPUTS)
+    learned = cm.node_costs(w)
+    prof = profile_costs(w, ins)
+    cp = abi.DAG_RANK_CRITICAL_PATH
+    out = {"workload": w.name, "priority": "critical path (upward + downward rank)", "makespan_us": {}}
+    for name, o in (("roofline_model", options(rank_form=cp)),
+                    ("profile", options(rank_form=cp, scheduler=abi.DAG_SCHED_RANK_GIVEN, node_cost_us=prof)),
+                    ("learned", options(rank_form=cp, scheduler=abi.DAG_SCHED_RANK_GIVEN, node_cost_us=learned)),
+                    ("fifo", options(scheduler=abi.DAG_SCHED_FIFO))):
+        d = Dag(w, o, resident_inputs=True)
+        d.set_inputs(ins)
+        d.run()
+        out["makespan_us"][name] = statistics.median(timed_fn(d, reps))
+        d.close()
+    ms = out["makespan_us"]
+    out["gain_learned_vs_roofline_model"] = ms["roofline_model"] / ms["learned"] - 1.0
+    out["regret_learned_vs_profile"] = ms["learned"] / ms["profile"] - 1.0
+    return out
 
 
 def serving_models():

@@ -144,8 +144,20 @@ typedef struct {
                                  trans_b = 0 (all with one shape) is kept transposed (N x K per batch) on
                                  the device, made from its given layout at upload, so the tensor cores read
                                  it K-major; 1: every buffer keeps the caller's layout */
-  int32_t reserved[1];
+  int32_t rank_form;          /* dag_rank_form: the priority the ranked queue orders ready tiles by */
 } dag_options;
+
+/* Ready-tile priority of the ranked schedulers (dag_options.rank_form).
+ * DAG_RANK_UPWARD (default): the bottom-level (upward) rank of the tile's
+ * kernel -- its cost plus the longest cost path to a sink -- as the paper's
+ * priority queue F orders task components (§5) and HEFT ranks kernels.
+ * DAG_RANK_CRITICAL_PATH: upward rank plus downward rank (the longest cost
+ * path from a root to the kernel), so every kernel of the longest path has
+ * the same, highest priority (the critical-path priority of CPOP, published
+ * beside HEFT); a long chain of short kernels then keeps its place ahead of
+ * wide independent work all along, where the upward rank lets it fall
+ * behind once its remaining length drops below the wide work's cost. */
+typedef enum { DAG_RANK_UPWARD = 0, DAG_RANK_CRITICAL_PATH = 1 } dag_rank_form;
 
 /* Epilogue fusion (dag_options.fuse).  DAG_FUSE_NONE (default): every kernel
  * runs its own tiles.  DAG_FUSE_ACT: activation kernels run in the epilogue

@@ -27,6 +27,7 @@ DAG_ACT_NONE, DAG_ACT_RELU, DAG_ACT_GELU = 0, 1, 2
 DAG_BUF_INPUT, DAG_BUF_OUTPUT, DAG_BUF_RESIDENT = 1, 2, 4
 DAG_SCHED_RANK_MODEL, DAG_SCHED_RANK_GIVEN, DAG_SCHED_FIFO = 0, 1, 2
 DAG_F32_GEMM_TENSOR, DAG_F32_GEMM_SIMT, DAG_F32_GEMM_TENSOR_NARROW, DAG_F32_GEMM_TENSOR_WIDE = 0, 1, 2, 3
+DAG_RANK_UPWARD, DAG_RANK_CRITICAL_PATH = 0, 1
 DAG_FUSE_NONE, DAG_FUSE_ACT, DAG_FUSE_ALL = 0, 1, 2
 DAG_TC_GIVEN, DAG_TC_WHOLE, DAG_TC_PER_KERNEL = 0, 1, 2
 
@@ -49,7 +50,7 @@ class dag_options(C.Structure):
     _fields_ = [("timeout_ns", u64), ("trace", i32), ("max_ctas", i32), ("scheduler", i32),
                 ("tile_override", i32), ("node_cost_us", C.POINTER(f32)), ("debug_never_ready", i32),
                 ("use_graph", i32), ("autotune", i32), ("f32_gemm", i32), ("split_k", i32), ("fuse", i32),
-                ("keep_layout", i32), ("reserved", i32 * 1)]
+                ("keep_layout", i32), ("rank_form", i32)]
 
 
 class dag_cq_options(C.Structure):

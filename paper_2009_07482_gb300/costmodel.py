@@ -28,7 +28,10 @@ import numpy as np
 from . import _binding as abi
 from .dag import Dag, describe, options
 
-N_FEATURES = 11
+N_FEATURES = 12
+# per-SM rates of the roofline feature (measured GB300 peaks / 152 SMs): bf16
+# tensor, f32 on the tensor cores as 3 x TF32, and HBM bandwidth
+_SM_BF16, _SM_F32, _SM_BW = 1.9e12 / 152, 0.31e12 / 152, 6.7e12 / 152
 STAMP_READY, STAMP_END = 1, 9
 
 
@@ -50,15 +53,22 @@ def _depths(w) -> List[int]:
 
 
 def features(w, tiles: np.ndarray, grid: int) -> np.ndarray:
-    """(n_nodes, 11) features: op kind one-hot (bf16 GEMM, f32 GEMM, add,
-    activation, softmax), log2 of M, N, K+1, tile area, tile count, and of
-    1 + (tiles at the kernel's depth level) / grid."""
+    """(n_nodes, 12) features: op kind one-hot (bf16 GEMM, f32 GEMM, add,
+    activation, softmax), log2 of M, N, K+1, tile area, tile count, of
+    1 + (tiles at the kernel's depth level) / grid, and of a tile's roofline
+    time on one SM (max of its flops over the SM's share of the tensor peak
+    and its bytes over its share of HBM bandwidth, in us): the network then
+    learns a correction to the roofline, which carries over to sizes it was
+    not trained on."""
     nn = len(w.nodes)
     count = np.bincount(tiles[:, 0], minlength=nn)
     area = np.zeros(nn)
+    trows = np.zeros(nn)
+    tcols = np.zeros(nn)
     for r in tiles:
         if area[r[0]] == 0:
             area[r[0]] = (r[2] - r[1]) * (r[4] - r[3])
+            trows[r[0]], tcols[r[0]] = r[2] - r[1], r[4] - r[3]
     dep = _depths(w)
     level = {}
     for v in range(nn):
@@ -81,6 +91,14 @@ def features(w, tiles: np.ndarray, grid: int) -> np.ndarray:
         F[v, 8] = math.log2(max(1.0, area[v]))
         F[v, 9] = math.log2(max(1, count[v]))
         F[v, 10] = math.log2(1.0 + level[dep[v]] / grid)
+        a = max(1.0, area[v])
+        if n.op == "gemm":
+            es = 2 if w.buffers[n.a].dtype == "bf16" else 4
+            t_flop = 2.0 * a * K / (_SM_BF16 if es == 2 else _SM_F32)
+            t_byte = ((trows[v] + tcols[v]) * K * es + a * 4) / _SM_BW
+        else:
+            t_flop, t_byte = 0.0, a * 3 * 4 / _SM_BW
+        F[v, 11] = math.log2(max(t_flop, t_byte) * 1e6 + 1e-3)
     return F
 
 

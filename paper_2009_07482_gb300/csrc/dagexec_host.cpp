@@ -918,6 +918,15 @@ static void order_tiles(Plan &P, const std::vector<std::vector<int>> &tile_pred)
     P.rank[v] = P.node_cost[v] + m;
   }
   const bool fifo = P.opt.scheduler == DAG_SCHED_FIFO;
+  // the queue's priority: the upward rank, or with DAG_RANK_CRITICAL_PATH the
+  // upward plus the downward rank (longest cost path from a root)
+  std::vector<double> prio(P.rank);
+  if (P.opt.rank_form == DAG_RANK_CRITICAL_PATH) {
+    std::vector<double> down(g.nn, 0.0);
+    for (int v : g.topo)
+      for (int w : g.succ[v]) down[w] = std::max(down[w], down[v] + P.node_cost[v]);
+    for (int v = 0; v < g.nn; ++v) prio[v] = P.rank[v] + down[v];
+  }
 
   std::vector<std::vector<int>> tile_succ(nt);
   std::vector<int> indeg(nt, 0);
@@ -929,7 +938,7 @@ static void order_tiles(Plan &P, const std::vector<std::vector<int>> &tile_pred)
   // available set ordered by (rank desc, kernel topo position, creation index)
   auto better = [&](int a, int b) {
     const int va = P.tiles[a].node, vb = P.tiles[b].node;
-    if (!fifo && P.rank[va] != P.rank[vb]) return P.rank[va] < P.rank[vb];
+    if (!fifo && prio[va] != prio[vb]) return prio[va] < prio[vb];
     if (g.topo_pos[va] != g.topo_pos[vb]) return g.topo_pos[va] > g.topo_pos[vb];
     return a > b;
   };

@@ -456,3 +456,33 @@ def concat(workloads: List[Workload], name: str = "batch") -> Workload:
 def random_batch(n_dags: int = 256, base_seed: int = 1000, **kw) -> List[Workload]:
     """The batched workload: seeded random layered DAGs, seed base_seed + i."""
     return [random_layered(base_seed + i, **kw) for i in range(n_dags)]
+
+
+def chain_and_fill(chain: int = 48, fill: int = 4, fill_dim: int = 4096, dtype: str = BF16, seed: int = 9) -> Workload:
+    """A latency-bound chain beside wide filler work: `chain` GEMMs
+    128 x 256 x 256 (+ReLU) in sequence -- one tile each, whose time is set by
+    per-tile latency rather than by their few flops -- and `fill` independent
+    fill_dim^3 GEMMs.  The chain is the critical path, but a roofline time
+    model prices each of its GEMMs at a fraction of its measured time, so
+    ranks from that model put the filler first.  Inputs U[-1,1), weights
+    N(0, 0.06) (chain) / N(0, 0.02) (filler)."""
+    w = Workload(f"chain{chain}_fill{fill}x{fill_dim}_{dtype}")
+    s = 0
+
+    def nxt():
+        nonlocal s
+        s += 1
+        return _seed(seed, s)
+
+    x = w.buf(128, 256, dtype, "input", ("uniform", nxt()), "x")
+    for i in range(chain):
+        W = w.buf(256, 256, dtype, "input", ("normal", nxt(), 0.06), f"Wc{i}")
+        last = i == chain - 1
+        y = w.buf(128, 256, F32 if last else dtype, "output" if last else "inter", name=f"c{i}")
+        w.node("gemm", x, y, b=W, act="relu", name=f"chain{i}")
+        x = y
+    for j in range(fill):
+        A = w.buf(fill_dim, fill_dim, dtype, "input", ("uniform", nxt()), f"F{j}")
+        B = w.buf(fill_dim, fill_dim, dtype, "input", ("normal", nxt(), 0.02), f"G{j}")
+        w.node("gemm", A, w.buf(fill_dim, fill_dim, F32, "output", name=f"H{j}"), b=B, name=f"fill{j}")
+    return w

@@ -92,3 +92,85 @@ def test_learned_costs_beat_untrained_and_roofline_estimates():
     costs = cm.node_costs(w)
     assert bits_equal(base, run_gpu(w, ins, opts=options(scheduler=abi.DAG_SCHED_RANK_GIVEN, node_cost_us=costs)))
     cm.close()
+
+
+def _training_traces():
+    """Tile times the executor recorded on random DAGs alone (sizes 64..4096)
+    and in batches of 2..32 (so the concurrency feature covers batched plans)."""
+    from synth.workloads import concat, random_batch
+    F, T = [], []
+    for i in range(16):
+        w = random_layered(5000 + i, 8, 24, 4, sizes=(64, 128, 256, 512, 1024, 2048, 4096))
+        f, t, *_ = measure(w, w.make_inputs())
+        F.append(f)
+        T.append(t)
+    seed = 7000
+    for k in (2, 8, 32):
+        w = concat(random_batch(k, base_seed=seed))
+        seed += k
+        f, t, *_ = measure(w, w.make_inputs())
+        F.append(f)
+        T.append(t)
+    return np.concatenate(F), np.concatenate(T)
+
+
+def test_learned_costs_put_a_latency_bound_chain_first_and_shorten_the_makespan():
+    """What the trained network gains over the planner's roofline model: on a
+    DAG whose critical path is a chain of 48 small GEMMs (latency-bound: the
+    roofline model prices each at a fraction of its measured time) beside four
+    4096^3 GEMMs, the learned costs -- like the measured profile, and unlike
+    the roofline model -- make the chain the most expensive path, and with the
+    critical-path priority the executor then runs the chain alongside the
+    filler instead of after it.  Medians of 9 runs; the gain must exceed the
+    runs' spread several times over."""
+    import statistics
+
+    import torch
+    from paper_2009_07482_gb300.costmodel import profile_costs
+    from synth.workloads import chain_and_fill
+    F, T = _training_traces()
+    cm = CostModel().fit(F, T)
+    w = chain_and_fill()
+    ins = w.make_inputs()
+    chain = [k for k, n in enumerate(w.nodes) if n.name.startswith("chain")]
+    fill = [k for k, n in enumerate(w.nodes) if n.name.startswith("fill")]
+    learned = cm.node_costs(w)
+    cm.close()
+    prof = profile_costs(w, ins)
+    d = Dag(w, options(), resident_inputs=True)
+    roof = abi.dag_node_costs_get(d.h).astype(float).tolist()
+    d.close()
+    path = lambda c: sum(c[k] for k in chain)
+    assert path(prof) > max(prof[k] for k in fill)        # measured: the chain is the longest path
+    assert path(learned) > max(learned[k] for k in fill)  # learned: the same
+    assert path(roof) < max(roof[k] for k in fill)        # roofline: the filler looks longer
+
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def makespans(costs):
+        o = options(rank_form=abi.DAG_RANK_CRITICAL_PATH)
+        if costs is not None:
+            o = options(rank_form=abi.DAG_RANK_CRITICAL_PATH, scheduler=abi.DAG_SCHED_RANK_GIVEN, node_cost_us=costs)
+        dd = Dag(w, o, resident_inputs=True)
+        dd.set_inputs(ins)
+        out = []
+        for i in range(12):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            dd.submit(stream.cuda_stream)
+            b.record(stream)
+            abi.check(dd.wait(), "wait")
+            if i >= 3:
+                out.append(a.elapsed_time(b) * 1e3)
+        dd.close()
+        return out
+
+    t_roof, t_learn, t_prof = makespans(None), makespans(learned), makespans(prof)
+    spread = max(max(x) - min(x) for x in (t_roof, t_learn, t_prof))
+    gain = statistics.median(t_roof) - statistics.median(t_learn)
+    assert gain > 4 * spread, (statistics.median(t_roof), statistics.median(t_learn), spread)
+    assert statistics.median(t_learn) < 0.85 * statistics.median(t_roof)
+    # the learned ranks come within 10 % of the measured profile's
+    assert statistics.median(t_learn) < 1.1 * statistics.median(t_prof)
