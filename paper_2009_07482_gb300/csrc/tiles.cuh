@@ -744,8 +744,6 @@ __device__ __forceinline__ void gemm_epilogue(const ExecParams &p, const TileDes
     // the two warps of a TMEM lane quadrant take alternate whole chunks
     // (a 64-column tile has a single bf16 chunk: the second warp idles)
     for (int c = half * step; c < BN; c += 2 * step) {
-      if (lane == 0) bulk_wait_read();  // the previous chunk's store has left the staging block
-      __syncwarp();
       for (int sub = 0; sub < step; sub += 32) {
         float v[32];
         tmem_ld32(trow + (uint32_t)(c + sub), v);
@@ -755,6 +753,12 @@ __device__ __forceinline__ void gemm_epilogue(const ExecParams &p, const TileDes
         if constexpr (kPost) {
           const int row = m0 + trow_local;
           post_ops(npg, v, (int64_t)bt * M + row, row < M, n0 + c + sub, N);
+        }
+        if (sub == 0) {
+          // only now wait for the previous chunk's store to leave the staging
+          // block: its read overlapped this chunk's TMEM load and arithmetic
+          if (lane == 0) bulk_wait_read();
+          __syncwarp();
         }
         // 16-byte chunk j of this row goes to position j ^ (row % 8) (128-byte swizzle)
         if (c_dt == 1) {
