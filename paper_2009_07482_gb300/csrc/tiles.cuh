@@ -165,16 +165,19 @@ __device__ __forceinline__ bool gemm_mma(const TileDesc &t, const NodeParams &np
     tc_fence_after();
     const uint32_t a0 = smem_u32(sA + st.idx * kStageA);
     const uint32_t b0 = smem_u32(sB + st.idx * kStageB);
+    // K-major, 128-byte swizzle: a K step of 16 bf16 is 32 bytes along the row.
+    // B MN-major: 16 K rows of 128 bytes = 2048 bytes per step, 64-column
+    // chunks 8 KiB apart (leading offset), 8-row groups 1 KiB apart (stride offset).
+    // The descriptors are built once per stage and stepped in their start
+    // address field (16-byte units; shared addresses stay below 2^18 bytes,
+    // so the 14-bit field never carries).
+    const uint64_t ad0 = smem_desc_sw128(a0, 16, 1024);
+    const uint64_t bd0 = trans_b ? smem_desc_sw128(b0, 16, 1024) : smem_desc_sw128(b0, 64 * kBK * 2, 1024);
+    const uint64_t bstep = trans_b ? 32 >> 4 : 2048 >> 4;
 #pragma unroll
-    for (int kk = 0; kk < kBK / 16; ++kk) {
-      // K-major, 128-byte swizzle: a K step of 16 bf16 is 32 bytes along the row.
-      // B MN-major: 16 K rows of 128 bytes = 2048 bytes per step, 64-column
-      // chunks 8 KiB apart (leading offset), 8-row groups 1 KiB apart (stride offset).
-      const uint64_t ad = smem_desc_sw128(a0 + kk * 32, 16, 1024);
-      const uint64_t bd = trans_b ? smem_desc_sw128(b0 + kk * 32, 16, 1024)
-                                  : smem_desc_sw128(b0 + kk * 2048, 64 * kBK * 2, 1024);
-      mma_bf16(tmem_d, ad, bd, idesc, (kb != kb0 || kk != 0) ? 1u : 0u);
-    }
+    for (int kk = 0; kk < kBK / 16; ++kk)
+      mma_bf16(tmem_d, ad0 + (uint64_t)(kk * (32 >> 4)), bd0 + (uint64_t)kk * bstep, idesc,
+               (kb != kb0 || kk != 0) ? 1u : 0u);
     mma_commit(&ctl->empty[st.idx]);
     st.next(kStages);
   }
@@ -319,12 +322,13 @@ __device__ __forceinline__ bool tf32_mma(const NodeParams &np, uint8_t *smem, Sm
     const uint32_t ahi = smem_u32(sA + st.idx * kStageA);
     const uint32_t bhi = smem_u32(sB + st.idx * kStageB);
     const uint32_t blo = bhi + kTf32Blo, alo = bhi + kTf32Alo;
+    const uint64_t dah0 = smem_desc_sw128(ahi, 16, 1024), dal0 = smem_desc_sw128(alo, 16, 1024);
+    const uint64_t dbh0 = smem_desc_sw128(bhi, 16, 1024), dbl0 = smem_desc_sw128(blo, 16, 1024);
 #pragma unroll
     for (int kk = 0; kk < kBKF / 8; ++kk) {
-      const uint64_t dah = smem_desc_sw128(ahi + kk * 32, 16, 1024);
-      const uint64_t dal = smem_desc_sw128(alo + kk * 32, 16, 1024);
-      const uint64_t dbh = smem_desc_sw128(bhi + kk * 32, 16, 1024);
-      const uint64_t dbl = smem_desc_sw128(blo + kk * 32, 16, 1024);
+      // a K step of 8 is 32 bytes: 2 in the descriptors' 16-byte address field
+      const uint64_t o = (uint64_t)(kk * 2);
+      const uint64_t dah = dah0 + o, dal = dal0 + o, dbh = dbh0 + o, dbl = dbl0 + o;
       // the small products first, then the large one
       mma_tf32(tmem_d, dal, dbh, idesc, kk != 0 ? 1u : 0u);
       mma_tf32(tmem_d, dah, dbl, idesc, 1u);
@@ -504,10 +508,13 @@ __device__ __forceinline__ bool tf32w_mma(const TileDesc &t, const NodeParams &n
     tc_fence_after();
     const uint32_t ahi = smem_u32(sA + st.idx * kStageA), alo = ahi + kBM * kBKW * 4;
     const uint32_t bhi = smem_u32(sB + st.idx * kStageB), blo = bhi + blo_off;
+    const uint64_t dah0 = smem_desc_sw64(ahi), dal0 = smem_desc_sw64(alo);
+    const uint64_t dbh0 = smem_desc_sw64(bhi), dbl0 = smem_desc_sw64(blo);
 #pragma unroll
     for (int kk = 0; kk < kBKW / 8; ++kk) {
-      const uint64_t dah = smem_desc_sw64(ahi + kk * 32), dal = smem_desc_sw64(alo + kk * 32);
-      const uint64_t dbh = smem_desc_sw64(bhi + kk * 32), dbl = smem_desc_sw64(blo + kk * 32);
+      // a K step of 8 is 32 bytes: 2 in the descriptors' 16-byte address field
+      const uint64_t o = (uint64_t)(kk * 2);
+      const uint64_t dah = dah0 + o, dal = dal0 + o, dbh = dbh0 + o, dbl = dbl0 + o;
       // the small products first, then the large one
       mma_tf32(dst, dal, dbh, idesc, (j % kWideP != 0 || kk != 0) ? 1u : 0u);
       mma_tf32(dst, dah, dbl, idesc, 1u);
