@@ -235,6 +235,31 @@ def test_wide_f32_tiles_between_other_tensor_tiles_in_one_cta():
         assert bits_equal(base, got)
 
 
+def test_wide_f32_single_partial_tiles_after_long_epilogues():
+    """256-column wide f32 tiles with one partial (K <= 128), each right
+    after a tile whose epilogue is long (GELU, bf16 out) or whose partials
+    are many, in one CTA and in three: the MMA issuer starts such a tile in
+    the buffer the previous one freed early and takes the other buffer's
+    release in turn, so the hand-over holds whichever side is first."""
+    w = Workload("wide_single_partial")
+    outs = []
+    for i, K in enumerate([64, 2048, 16, 128, 1024, 48, 64]):
+        A = w.buf(2048, K, F32, "input", ("uniform", 80 + i))
+        B = w.buf(512, K, F32, "input", ("uniform", 90 + i))
+        C = w.buf(2048, 512, BF16 if K >= 1024 else F32, "output")
+        w.node("gemm", A, C, b=B, trans_b=1, act="gelu" if K >= 1024 else "relu")
+        outs.append(C)
+    wide = abi.DAG_F32_GEMM_TENSOR_WIDE
+    base = None
+    for o in (options(trace=1, max_ctas=1, f32_gemm=wide, tile_override=256, split_k=1),
+              options(trace=1, max_ctas=3, f32_gemm=wide, tile_override=256, split_k=1)):
+        tiles, got = _resident_roundtrip(w, o)
+        assert set((tiles[:, 5] & 0xFFFF).tolist()) == {256}
+        if base is None:
+            base = got
+        assert bits_equal(base, got)
+
+
 def test_f32_unaligned_view_runs_on_simt_tiles():
     w = Workload("f32_view")
     P = w.buf(256, 100, F32, "input", ("uniform", 1))
