@@ -561,6 +561,8 @@ typedef struct {
   double work_bound_us;          /* max(critical path, total flops/peak, total bytes/bw) */
   int32_t tile_override, scheduler;  /* the plan's tile policy and queue order (the autotuner's choice) */
   double tuned_us;               /* autotune: measured makespan of the chosen plan (0 if not tuned) */
+  double buffer_bytes;           /* device memory of the handle's buffers (every buffer at its row pitch, a
+                                    weight kept transposed in its N x K form); 0 for caller-owned buffers */
 } dag_plan_info;
 
 dag_status dag_plan_get(dag_handle *h, dag_plan_info *out);

@@ -86,7 +86,8 @@ class dag_trace_record(C.Structure):
 class dag_plan_info(C.Structure):
     _fields_ = [("n_tiles", i32), ("n_counters", i32), ("n_waits", i32), ("grid", i32), ("smem_bytes", i32),
                 ("flops", C.c_double), ("bytes", C.c_double), ("critical_path_us", C.c_double),
-                ("work_bound_us", C.c_double), ("tile_override", i32), ("scheduler", i32), ("tuned_us", C.c_double)]
+                ("work_bound_us", C.c_double), ("tile_override", i32), ("scheduler", i32), ("tuned_us", C.c_double),
+                ("buffer_bytes", C.c_double)]
 
 
 class dag_batch_item(C.Structure):

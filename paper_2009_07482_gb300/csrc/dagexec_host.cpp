@@ -642,6 +642,12 @@ static void choose_split(Plan &P) {
       kit = (g.K[v] + kBKW - 1) / kBKW;
       if (lt * 2 > P.n_sm || kit < 32) continue;
       S = std::min({4, (int)(P.n_sm / std::max(1L, lt)), kit / 16});
+    } else if (P.tf32[v]) {
+      // the 128 x 64 f32 form: a K block (32 deep) takes ~0.85 us, so a level
+      // of few tiles with K >= 256 gains from partials of 2+ blocks each
+      kit = (g.K[v] + kBKF - 1) / kBKF;
+      if (lt * 2 > P.n_sm || kit < 8) continue;
+      S = std::min({4, (int)(P.n_sm / std::max(1L, lt)), kit / 2});
     } else {
       continue;
     }
@@ -1075,6 +1081,7 @@ struct dag_handle {
   int device = 0;
   // device memory
   void *arena = nullptr;      // buffers
+  size_t arena_bytes = 0;
   void *meta = nullptr;       // plan arrays
   float *split_scratch = nullptr;  // split K partial sums
   void *staging = nullptr;         // upload area of weights kept transposed
@@ -1295,6 +1302,7 @@ static dag_status create_impl(const dag_node_desc *nodes, int n_nodes, const dag
     return fail(DAG_ENOMEM, "weight staging (%zu bytes)", stage_bytes);
   }
   if (total && cudaMalloc(&h->arena, total) != cudaSuccess) { free_handle(h); return fail(DAG_ENOMEM, "device buffers (%zu bytes)", total); }
+  h->arena_bytes = total;
   if (total) cudaMemset(h->arena, 0, total);
   for (int b = 0; b < g.nb; ++b) {
     const int r = g.root[b];
@@ -1814,6 +1822,7 @@ extern "C" dag_status dag_plan_get(dag_handle *h, dag_plan_info *o) {
   o->tile_override = h->P.opt.tile_override;
   o->scheduler = h->P.opt.scheduler;
   o->tuned_us = h->tuned_us;
+  o->buffer_bytes = (double)h->arena_bytes;
   return DAG_OK;
 }
 

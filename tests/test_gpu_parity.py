@@ -260,6 +260,46 @@ def test_wide_f32_single_partial_tiles_after_long_epilogues():
         assert bits_equal(base, got)
 
 
+@pytest.mark.parametrize("K,bn", [(16, 256), (200, 128), (2048, 256), (1000, 128)])
+def test_wide_f32_weight_kept_k_major_matches_the_callers_k_major_copy(K, bn):
+    """A resident f32 weight W (K x N, trans_b = 0) is kept K-major on the
+    device, made at upload, so that wide f32 tiles can read it.  The same
+    GEMM over the caller's own K-major copy W^T (trans_b = 1) gives the same
+    bits; both match the oracle, and the transposed copy takes exactly the
+    device memory of the caller's N x K form."""
+    M, N = 640, 512
+    outs = {}
+    mem = {}
+    for form in ("kn", "nk"):
+        w = Workload("k_major_" + form)
+        A = w.buf(M, K, F32, "input", ("uniform", 11))
+        W = w.buf(K, N, F32, "input", ("uniform", 12)) if form == "kn" else w.buf(N, K, F32, "input")
+        C = w.buf(M, N, F32, "output")
+        w.node("gemm", A, C, b=W, trans_b=0 if form == "kn" else 1, act="relu")
+        if form == "kn":
+            ins = w.make_inputs()
+        else:
+            ins = {A: base_ins[A], W: np.ascontiguousarray(base_ins[W].T)}
+        ref = oracle.run(w, ins)
+        d = Dag(w, options(trace=1, f32_gemm=abi.DAG_F32_GEMM_TENSOR_WIDE, tile_override=bn, split_k=1),
+                resident_inputs=True)
+        try:
+            assert set((d.tiles()[:, 5] & 0xFFFF).tolist()) == {bn}
+            d.set_inputs(ins)
+            d.run()
+            got = {C: d.output(C)}
+            compare(w, got, ref)
+            check_trace(w, d)
+            outs[form] = got[C]
+            mem[form] = abi.dag_plan_get(d.h).buffer_bytes
+        finally:
+            d.close()
+        if form == "kn":
+            base_ins = ins
+    assert np.array_equal(outs["kn"].view(np.uint32), outs["nk"].view(np.uint32))
+    assert mem["kn"] == mem["nk"] > 0
+
+
 def test_f32_unaligned_view_runs_on_simt_tiles():
     w = Workload("f32_view")
     P = w.buf(256, 100, F32, "input", ("uniform", 1))
