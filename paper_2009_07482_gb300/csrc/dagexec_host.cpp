@@ -642,12 +642,6 @@ static void choose_split(Plan &P) {
       kit = (g.K[v] + kBKW - 1) / kBKW;
       if (lt * 2 > P.n_sm || kit < 32) continue;
       S = std::min({4, (int)(P.n_sm / std::max(1L, lt)), kit / 16});
-    } else if (P.tf32[v]) {
-      // the 128 x 64 f32 form: a K block (32 deep) takes ~0.85 us, so a level
-      // of few tiles with K >= 256 gains from partials of 2+ blocks each
-      kit = (g.K[v] + kBKF - 1) / kBKF;
-      if (lt * 2 > P.n_sm || kit < 8) continue;
-      S = std::min({4, (int)(P.n_sm / std::max(1L, lt)), kit / 2});
     } else {
       continue;
     }

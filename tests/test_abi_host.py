@@ -233,6 +233,25 @@ def _noalloc_status(bufs, ptrs, pitch):
     return abi.dag_run_noalloc(nodes, bufs, ptrs, pitch, None, 0)
 
 
+@pytest.mark.parametrize("seed", [6000, 6001, 6002])
+def test_split_k_only_where_the_tile_form_runs_a_share_of_k(seed):
+    """Split K is planned for bf16 tiles and the wide f32 form, whose device
+    loops take their share of the K blocks; the 128 x 64 f32 tiles and the
+    SIMT f32 tiles always run the whole K loop, so a plan never splits them
+    (a split there would sum S whole-K products)."""
+    for w in (random_layered(seed, 8, 24, 4, sizes=(64, 128, 256, 512, 1024)), fork_join(256)):
+        for res in (False, True):
+            n, e, b = dagmod.describe(w, resident_inputs=res)
+            t, _ = abi.dag_plan_host(n, e, b, dagmod.options(), 152)
+            for row in t:
+                node = w.nodes[int(row[0])]
+                split = int(row[5]) >> 16
+                if node.op != "gemm" or not split:
+                    continue
+                bf16 = w.buffers[node.a].dtype == BF16
+                assert bf16 or (int(row[5]) & 0xFFFF) in (128, 256), (w.name, int(row[0]), int(row[5]) & 0xFFFF)
+
+
 def test_no_alloc_rejects_overlapping_root_buffers():
     """dag_run_noalloc: two root buffers sharing device memory (an output
     placed on an input, or rows of one falling inside another) are rejected
