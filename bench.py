@@ -9,7 +9,8 @@ weights and activations resident in HBM; L2 is flushed (a 256 MiB write)
 between timed steps, outside the timed events.
 
 Also measured and reported on the same JSON line:
-  coarse     the same tiles launched kernel by kernel on one stream
+  coarse     every kernel as given (no sibling GEMMs merged), its tiles
+             launched kernel by kernel on one stream
   epilogue_fusion  the persistent executor with the opt-in epilogue fusion
              modes, when the DAG has kernels they would fuse (single DAGs)
   e2e        the same metric through the C ABI with host buffers: upload of
@@ -218,7 +219,12 @@ def run_exp1(args):
                         out.append(a.elapsed_time(b) * 1e3)
                 return statistics.median(out)
 
-            row = {"heads": H, "persistent_us": timed(d.submit, 30), "coarse_us": timed(d.submit_coarse, 10)}
+            row = {"heads": H, "persistent_us": timed(d.submit, 30)}
+            d.close()
+            # the paper's forms run every kernel as given: no sibling GEMMs merged
+            d = Dag(w, options(merge=1), resident_inputs=True)
+            d.set_inputs(w.make_inputs(_INPUTS))
+            row["coarse_us"] = timed(d.submit_coarse, 10)
             row.update(paper_alg1(d, abi, reps=6))
             row["speedup_persistent_over_best"] = row["best_us"] / row["persistent_us"]
             rows.append(row)
@@ -242,6 +248,9 @@ def run_exp1(args):
                 if i >= 3:
                     pers.append(a.elapsed_time(b) * 1e3)
             row = {"beta": beta, "persistent_us": statistics.median(pers)}
+            d.close()
+            d = Dag(w, options(merge=1), resident_inputs=True)  # Alg. 1 runs every kernel as given
+            d.set_inputs(w.make_inputs(_INPUTS))
             clus = {q: statistics.median(d.run_cq(n_queues=q, components=abi.DAG_TC_GIVEN).device_us
                                          for _ in range(4)) for q in (1, 2, 3, 4, 5)}
             row["clustering_best_q"] = min(clus, key=clus.get)
@@ -951,9 +960,15 @@ def config_extras(args, abi, Dag, options, stream, flush, peaks, peaks_src, reps
         d.set_inputs(w.make_inputs(_INPUTS))
         d.run()
         fine = timed(d.submit, d, max(reps, args.steps))
-        coarse = timed(d.submit_coarse, d, max(5, reps // 2))
-        alg1 = paper_alg1(d, abi, reps=5)
         info = d.plan()
+        # the kernel-by-kernel path and Alg. 1 launch every kernel as given (no
+        # sibling GEMMs merged), as the paper's forms do
+        dk = Dag(w, options(merge=1), resident_inputs=True)
+        dk.set_inputs(w.make_inputs(_INPUTS))
+        dk.run()
+        coarse = timed(dk.submit_coarse, dk, max(5, reps // 2))
+        alg1 = paper_alg1(dk, abi, reps=5)
+        dk.close()
         med = statistics.median(fine)
         roof, _ = roofline_of(w, info, statistics.mean(fine), peaks, peaks_src, False)
         out[name] = {"workload": desc, "tiles": info.n_tiles,
@@ -1014,9 +1029,9 @@ def main():
     X_ids = [i for i in w.input_ids() if i not in weights]
     Y_ids = w.output_ids()
 
-    def make_dag(streamed, fuse=0, trace=0):
+    def make_dag(streamed, fuse=0, trace=0, merge=0):
         o = options(use_graph=1 if batched else 0, f32_gemm=abi.DAG_F32_GEMM_SIMT if args.f32_simt else 0,
-                    fuse=fuse, trace=trace)
+                    fuse=fuse, trace=trace, merge=merge)
         if batched:
             return Dag.batch(wl, o, resident_inputs=not streamed, streamed=set(X_ids) if streamed else None)
         return Dag(w, o, streamed=set(X_ids)) if streamed else Dag(w, o, resident_inputs=True)
@@ -1074,10 +1089,16 @@ def main():
         print(json.dumps({"timeline": args.workload, "config": {"workload": desc},
                           "untraced_makespan_us_median": round(statistics.median(fine_us), 2), **tl}))
         return 0
-    coarse_us, _ = timed(d.submit_coarse, min(10, max(3, args.steps // 4)) if batched else max(10, args.steps // 4), 3)
-    # kernel-by-kernel launches: one per kernel not fused into a GEMM, two for a split GEMM
-    fused = d.fusion()
-    tl = d.tiles()
+    # kernel by kernel: every kernel as given (no sibling GEMMs merged), one
+    # launch per kernel not fused into a GEMM, two for a split GEMM
+    dk = make_dag(False, merge=1)
+    dk.set_inputs(ins)
+    dk.run()
+    coarse_us, _ = timed(dk.submit_coarse, min(10, max(3, args.steps // 4)) if batched else max(10, args.steps // 4), 3,
+                         dd=dk)
+    fused = dk.fusion()
+    tl = dk.tiles()
+    dk.close()
     split_nodes = {int(t[0]) for t in tl if (int(t[5]) >> 16) & 0xFF}
     n_coarse_launches = sum(1 + (v in split_nodes) for v in range(len(w.nodes)) if fused[v] < 0)
     # the opt-in epilogue-fusion modes (the measured line runs without fusion)

@@ -145,6 +145,13 @@ typedef struct {
                                  the device, made from its given layout at upload, so the tensor cores read
                                  it K-major; 1: every buffer keeps the caller's layout */
   int32_t rank_form;          /* dag_rank_form: the priority the ranked queue orders ready tiles by */
+  int32_t merge;              /* 0: sibling GEMMs -- one task component, one A (trans_b = 0, batch 1), one
+                                 K, activation and scale, each narrower than 256 columns, with resident
+                                 weights (and biases) only they read and private intermediate outputs --
+                                 run as one GEMM over their summed width: their weights, biases and
+                                 outputs are laid out as column slices of parent buffers (see
+                                 dag_merge_get; bit-identical results).  1: every GEMM keeps its own
+                                 tiles.  keep_layout = 1 implies 1. */
 } dag_options;
 
 /* Ready-tile priority of the ranked schedulers (dag_options.rank_form).
@@ -566,6 +573,16 @@ typedef struct {
 } dag_plan_info;
 
 dag_status dag_plan_get(dag_handle *h, dag_plan_info *out);
+
+/* Sibling GEMMs merged by the planner (dag_options.merge): per kernel v,
+ * leader[v] = the kernel whose tiles compute it (itself for that kernel; -1
+ * if v keeps its own tiles) and col_offset[v] = its first column in the
+ * merged GEMM's output (0 if not merged).  The merged kernel's tiles (its id
+ * in dag_tiles_get and the trace) cover the summed width.  cap entries at
+ * most; *n = kernel count.  dag_merge_host: the same without a device. */
+dag_status dag_merge_get(dag_handle *h, int32_t *leader, int32_t *col_offset, int cap, int *n);
+dag_status dag_merge_host(const dag_node_desc *nodes, int n_nodes, const dag_buffer_desc *buffers, int n_buffers,
+                          const dag_options *opts, int32_t *leader, int32_t *col_offset);
 
 /* Per-kernel costs (us) the plan's ranks were computed from: the roofline
  * time model's, or node_cost_us as given; n = kernel count. */

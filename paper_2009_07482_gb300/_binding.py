@@ -50,7 +50,7 @@ class dag_options(C.Structure):
     _fields_ = [("timeout_ns", u64), ("trace", i32), ("max_ctas", i32), ("scheduler", i32),
                 ("tile_override", i32), ("node_cost_us", C.POINTER(f32)), ("debug_never_ready", i32),
                 ("use_graph", i32), ("autotune", i32), ("f32_gemm", i32), ("split_k", i32), ("fuse", i32),
-                ("keep_layout", i32), ("rank_form", i32)]
+                ("keep_layout", i32), ("rank_form", i32), ("merge", i32)]
 
 
 class dag_cq_options(C.Structure):
@@ -139,6 +139,9 @@ _SIGS = {
                             C.POINTER(dag_buffer_desc), C.c_int, C.POINTER(dag_options), C.c_int,
                             C.POINTER(i32), C.c_int, C.POINTER(C.c_int), C.POINTER(dag_plan_info)]),
     "dag_fusion_get": (i32, [C.c_void_p, C.POINTER(i32), C.c_int, C.POINTER(C.c_int)]),
+    "dag_merge_get": (i32, [C.c_void_p, C.POINTER(i32), C.POINTER(i32), C.c_int, C.POINTER(C.c_int)]),
+    "dag_merge_host": (i32, [C.POINTER(dag_node_desc), C.c_int, C.POINTER(dag_buffer_desc), C.c_int,
+                             C.POINTER(dag_options), C.POINTER(i32), C.POINTER(i32)]),
     "dag_fusion_host": (i32, [C.POINTER(dag_node_desc), C.c_int, C.POINTER(dag_edge), C.c_int,
                               C.POINTER(dag_buffer_desc), C.c_int, C.POINTER(dag_options), C.POINTER(i32)]),
     "dag_set_peaks": (None, [C.c_double, C.c_double, C.c_double]),
@@ -275,6 +278,25 @@ def dag_fusion_get(h):
     out = (i32 * max(1, n.value))()
     check(lib().dag_fusion_get(h, out, n.value, C.byref(n)), "dag_fusion_get")
     return list(out[:n.value])
+
+
+def dag_merge_get(h):
+    """Per kernel: (the kernel whose tiles compute it or -1, its first column
+    in that merged GEMM) (see dag_merge_get in dagexec.h)."""
+    n = C.c_int(0)
+    check(lib().dag_merge_get(h, None, None, 0, C.byref(n)), "dag_merge_get")
+    lead, off = (i32 * max(1, n.value))(), (i32 * max(1, n.value))()
+    check(lib().dag_merge_get(h, lead, off, n.value, C.byref(n)), "dag_merge_get")
+    return list(lead[:n.value]), list(off[:n.value])
+
+
+def dag_merge_host(nodes, buffers, options: Optional[dag_options] = None):
+    """dag_merge_get without a device: the planner's merge of sibling GEMMs."""
+    na, nn = _arr(dag_node_desc, nodes)
+    ba, nb = _arr(dag_buffer_desc, buffers)
+    lead, off = (i32 * max(1, nn))(), (i32 * max(1, nn))()
+    check(lib().dag_merge_host(na, nn, ba, nb, C.byref(options) if options else None, lead, off), "dag_merge_host")
+    return list(lead[:nn]), list(off[:nn])
 
 
 def dag_set_input(h, buf: int, host_ptr) -> None:

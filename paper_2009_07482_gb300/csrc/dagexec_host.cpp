@@ -20,6 +20,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <tuple>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -379,6 +380,13 @@ struct Plan {
   std::vector<int> t_batch, t_K, t_N;   // its per-batch shape as given (K x N)
   bool allow_layout = true;             // not for caller-owned buffers (the no-alloc entry point)
   std::vector<int> absorbed_by;         // per node: the GEMM whose epilogue computes it, or -1
+  std::vector<int> merged_into;         // per node: the sibling GEMM whose tiles compute it as a column
+                                        // slice of a merged GEMM (itself for that GEMM), or -1
+  std::vector<int> merge_coff;          // per node of a merged group: its first column in the merged GEMM
+  bool merged_done = false;             // the graph's sibling GEMMs have been merged (once per plan)
+  std::vector<char> merge_parent;       // per buffer: a parent made for merged siblings' slices
+  std::vector<dag_node_desc> orig_nodes;  // the kernels as given (empty: no merge), for the DAG's own
+  std::vector<int> orig_N;                // algorithmic work and roofline
   std::vector<std::vector<int>> post;   // per GEMM: elementwise kernels fused into its epilogue, in order
   bool allow_split = true;              // split K needs scratch memory (not in the no-alloc entry point)
   std::vector<TileDesc> tiles;          // node-major creation order
@@ -437,6 +445,138 @@ static int ntiles_gemm(const Graph &g, int v, int bm, int bn) {
   return g.nodes[v].batch * ((g.M[v] + bm - 1) / bm) * ((g.N[v] + bn - 1) / bn);
 }
 
+// a node whose tiles another (merged) GEMM computes
+static inline bool merged_away(const Plan &P, int v) {
+  return !P.merged_into.empty() && P.merged_into[v] >= 0 && P.merged_into[v] != v;
+}
+
+// Sibling GEMMs merged by column slices (dag_options.merge = 0).  GEMMs of
+// one task component that read the same A with trans_b = 0, batch 1, one K,
+// activation and scale, each with a resident weight (and all or none with a
+// resident bias) that no other kernel reads and that no view covers, and with
+// a private intermediate output that no view covers, each narrower than 256
+// columns in 16-byte slices: their weights, biases and outputs become
+// column-slice views of three new parent buffers, and the first of them in
+// topological order computes the parent GEMM over the summed width.  A
+// tcgen05.mma of M = 128 takes 128 clocks for any N up to 128 and 166 for N
+// = 256, so N = 64 kernels run their tensor cores at a third of the rate that
+// one wide GEMM reaches.  Every output element is the same dot product in the
+// same K order, so the results are bit-identical; the dependency counters,
+// kept per root row block, see the views as they see every view.  The
+// merged GEMM inherits the successors of all its siblings (Alg. 1's task
+// components keep their order), and the siblings keep no tiles of their own.
+static void choose_merges(Plan &P) {
+  if (P.merged_done) return;
+  P.merged_done = true;
+  Graph &g = P.g;
+  P.merged_into.assign(g.nn, -1);
+  P.merge_coff.assign(g.nn, 0);
+  P.merge_parent.assign(g.nb, 0);
+  if (!P.allow_layout || P.opt.keep_layout || P.opt.merge == 1) return;
+  const int nb0 = g.nb;
+  std::vector<int> readers(nb0, 0);
+  std::vector<char> viewed(nb0, 0);
+  for (int b = 0; b < nb0; ++b)
+    if (g.bufs[b].view_of >= 0) viewed[g.root[b]] = 1;
+  for (int v = 0; v < g.nn; ++v) {
+    int in[3];
+    const int k = g.inputs(v, in);
+    for (int q = 0; q < k; ++q) readers[in[q]]++;
+  }
+  const uint32_t res = DAG_BUF_INPUT | DAG_BUF_RESIDENT;
+  auto private_weight = [&](int b) {
+    const dag_buffer_desc &d = g.bufs[b];
+    return d.view_of < 0 && !viewed[b] && readers[b] == 1 && (d.flags & (res | DAG_BUF_OUTPUT)) == res;
+  };
+  struct Cand {
+    int a, comp, K, M, act, bdt, odt, bias, biasdt;
+    uint32_t scale;
+    int pos, v;
+  };
+  std::vector<Cand> c;
+  for (int v = 0; v < g.nn; ++v) {
+    const dag_node_desc &n = g.nodes[v];
+    if (n.op != DAG_OP_GEMM || n.batch != 1 || n.trans_b || g.N[v] >= 256) continue;
+    const dag_buffer_desc &O = g.bufs[n.out];
+    const int ob = esize(O.dtype), bb = esize(g.bufs[n.b].dtype);
+    if (!private_weight(n.b) || (n.bias >= 0 && !private_weight(n.bias))) continue;
+    if (O.view_of >= 0 || viewed[n.out] || (O.flags & (DAG_BUF_INPUT | DAG_BUF_OUTPUT))) continue;
+    if ((g.N[v] * ob) % 16 || (g.N[v] * bb) % 16) continue;
+    uint32_t sc;
+    memcpy(&sc, &n.scale, 4);
+    c.push_back(Cand{n.a, n.component, g.K[v], g.M[v], n.act, g.bufs[n.b].dtype, O.dtype, n.bias >= 0,
+                     n.bias >= 0 ? g.bufs[n.bias].dtype : -1, sc, g.topo_pos[v], v});
+  }
+  auto key = [](const Cand &x) {
+    return std::make_tuple(x.a, x.comp, x.K, x.M, x.act, x.bdt, x.odt, x.bias, x.biasdt, x.scale);
+  };
+  std::sort(c.begin(), c.end(), [&](const Cand &x, const Cand &y) {
+    return key(x) != key(y) ? key(x) < key(y) : x.pos < y.pos;
+  });
+  auto add_buf = [&](int rows, int cols, int dtype, uint32_t flags) {
+    dag_buffer_desc d{};
+    d.rows = rows;
+    d.cols = cols;
+    d.dtype = dtype;
+    d.flags = flags;
+    d.view_of = -1;
+    d.col_offset = 0;
+    g.bufs.push_back(d);
+    g.root.push_back(g.nb);
+    g.coff.push_back(0);
+    P.merge_parent.push_back(1);
+    return g.nb++;
+  };
+  auto make_view = [&](int b, int parent, int off) {
+    g.bufs[b].view_of = parent;
+    g.bufs[b].col_offset = off;
+    g.root[b] = parent;
+    g.coff[b] = off;
+  };
+  for (size_t i = 0; i < c.size();) {
+    size_t j = i + 1;
+    while (j < c.size() && key(c[j]) == key(c[i])) ++j;
+    if (j - i >= 2) {
+      if (P.orig_nodes.empty()) {
+        P.orig_nodes = g.nodes;
+        P.orig_N = g.N;
+      }
+      const int L = c[i].v;  // the first in topological order computes the group
+      int total = 0;
+      for (size_t q = i; q < j; ++q) total += g.N[c[q].v];
+      const int Bp = add_buf(g.K[L], total, c[i].bdt, res);
+      const int Op = add_buf(g.M[L], total, c[i].odt, 0);
+      const int Cp = c[i].bias ? add_buf(1, total, c[i].biasdt, res) : -1;
+      int off = 0;
+      std::vector<int> succ;
+      for (size_t q = i; q < j; ++q) {
+        const int v = c[q].v;
+        const dag_node_desc &n = g.nodes[v];
+        make_view(n.b, Bp, off);
+        make_view(n.out, Op, off);
+        if (Cp >= 0) make_view(n.bias, Cp, off);
+        P.merged_into[v] = L;
+        P.merge_coff[v] = off;
+        off += g.N[v];
+        succ.insert(succ.end(), g.succ[v].begin(), g.succ[v].end());
+      }
+      dag_node_desc &ml = g.nodes[L];
+      ml.b = Bp;
+      ml.out = Op;
+      ml.bias = Cp;
+      g.N[L] = total;
+      for (int w : succ)
+        if (std::find(g.succ[L].begin(), g.succ[L].end(), w) == g.succ[L].end()) {
+          g.succ[L].push_back(w);
+          g.pred[w].push_back(L);
+        }
+      std::sort(g.succ[L].begin(), g.succ[L].end());
+      for (int w : succ) std::sort(g.pred[w].begin(), g.pred[w].end());
+    }
+    i = j;
+  }
+}
+
 // tile shapes: bf16 GEMMs take the widest BN (256/128/64) that still gives
 // the kernel's concurrency level enough tiles to fill the GPU; f32 GEMMs
 // likewise among 128x128 / 128x64 / 64x64.
@@ -469,6 +609,7 @@ static void choose_configs(Plan &P) {
     std::vector<long> level(maxd + 1, 0);
     for (int v = 0; v < nn; ++v) {
       const dag_node_desc &n = g.nodes[v];
+      if (merged_away(P, v)) continue;
       if (n.op != DAG_OP_GEMM) { level[depth[v]] += 8; continue; }
       if (P.tf32w[v]) level[depth[v]] += ntiles_gemm(g, v, 128, wbns[pass]);
       else if (P.tf32[v]) level[depth[v]] += ntiles_gemm(g, v, 128, kTf32BN);
@@ -534,10 +675,11 @@ static void choose_layouts(Plan &P) {
   P.t_N.assign(g.nb, 0);
   if (!P.allow_layout || P.opt.keep_layout) return;
   std::vector<char> ok(g.nb, 1);
-  for (int b = 0; b < g.nb; ++b)
-    if (g.root[b] != b) ok[g.root[b]] = 0;  // read through a view
+  for (int b = 0; b < g.nb; ++b)  // read through a view (the slices of merged siblings' weights aside:
+    if (g.root[b] != b && !P.merge_parent[g.root[b]]) ok[g.root[b]] = 0;  // uploaded slice by slice)
   std::vector<int> readers(g.nb, 0);
   for (int v = 0; v < g.nn; ++v) {
+    if (merged_away(P, v)) continue;
     const dag_node_desc &n = g.nodes[v];
     int in[3];
     const int k = g.inputs(v, in);
@@ -621,6 +763,7 @@ static void choose_split(Plan &P) {
   std::vector<long> level(nn + 1, 0);
   for (int v = 0; v < nn; ++v) {
     const dag_node_desc &n = g.nodes[v];
+    if (merged_away(P, v)) continue;
     if (n.op != DAG_OP_GEMM) {
       if (P.absorbed_by[v] < 0) level[depth[v]] += 8;
       continue;
@@ -630,7 +773,7 @@ static void choose_split(Plan &P) {
   }
   for (int v = 0; v < nn; ++v) {
     const dag_node_desc &n = g.nodes[v];
-    if (n.op != DAG_OP_GEMM) continue;
+    if (n.op != DAG_OP_GEMM || merged_away(P, v)) continue;
     const long lt = level[depth[v]];
     int S = 0, kit = 0;
     if (g.bufs[n.a].dtype == DAG_BF16) {
@@ -680,8 +823,8 @@ static void make_tiles(Plan &P) {
       P.tiles.push_back(t);
     };
     const int R = g.bufs[n.out].rows, C = g.bufs[n.out].cols;
-    if (P.absorbed_by[v] >= 0) {
-      // computed by its GEMM's tiles
+    if (P.absorbed_by[v] >= 0 || merged_away(P, v)) {
+      // computed by its GEMM's tiles, or by those of the sibling it is merged into
     } else if (n.op == DAG_OP_GEMM) {
       const bool bf = g.bufs[n.a].dtype == DAG_BF16;
       const int op = bf ? T_GEMM_BF16 : P.tf32w[v] ? T_GEMM_TF32W : P.tf32[v] ? T_GEMM_TF32 : T_GEMM_F32;
@@ -981,16 +1124,19 @@ static void roofline(Plan &P) {
   Graph &g = P.g;
   std::vector<double> cost(g.nn, 0.0);
   P.flops = P.bytes = 0;
+  // the DAG's own work: merged siblings count as the kernels they were given as
+  const std::vector<dag_node_desc> &nodes = P.orig_nodes.empty() ? g.nodes : P.orig_nodes;
+  const std::vector<int> &Ns = P.orig_N.empty() ? g.N : P.orig_N;
   for (int v = 0; v < g.nn; ++v) {
-    const dag_node_desc &n = g.nodes[v];
+    const dag_node_desc &n = nodes[v];
     double f = 0, b = 0;
-    int in[3];
-    const int k = g.inputs(v, in);
+    const int in[3] = {n.a, n.b, n.bias};
+    const int k = n.op == DAG_OP_GEMM ? (n.bias >= 0 ? 3 : 2) : n.op == DAG_OP_ADD ? 2 : 1;
     for (int q = 0; q < k; ++q) b += (double)g.bufs[in[q]].rows * g.bufs[in[q]].cols * esize(g.bufs[in[q]].dtype);
     b += (double)g.bufs[n.out].rows * g.bufs[n.out].cols * esize(g.bufs[n.out].dtype);
     double peak;
     if (n.op == DAG_OP_GEMM) {
-      f = 2.0 * n.batch * (double)g.M[v] * g.N[v] * g.K[v];
+      f = 2.0 * n.batch * (double)g.M[v] * Ns[v] * g.K[v];
       peak = (g.bufs[n.a].dtype == DAG_BF16 ? g_bf16_tflops : P.tf32[v] ? tf32x3_tflops() : g_f32_tflops) * 1e12;
     } else {
       f = (double)g.bufs[n.out].rows * g.bufs[n.out].cols;
@@ -1011,9 +1157,10 @@ static void roofline(Plan &P) {
   P.cp_us = cp;
   double f_bf = 0, f_tc = 0, f_32 = 0;
   for (int v = 0; v < g.nn; ++v)
-    if (g.nodes[v].op == DAG_OP_GEMM) {
-      const double f = 2.0 * g.nodes[v].batch * (double)g.M[v] * g.N[v] * g.K[v];
-      (g.bufs[g.nodes[v].a].dtype == DAG_BF16 ? f_bf : P.tf32[v] ? f_tc : f_32) += f;
+    if (nodes[v].op == DAG_OP_GEMM) {
+      const double f = 2.0 * nodes[v].batch * (double)g.M[v] * Ns[v] * g.K[v];
+      const int tv = merged_away(P, v) ? P.merged_into[v] : v;
+      (g.bufs[nodes[v].a].dtype == DAG_BF16 ? f_bf : P.tf32[tv] ? f_tc : f_32) += f;
     }
   const double work =
       (f_bf / (g_bf16_tflops * 1e12) + f_tc / (tf32x3_tflops() * 1e12) + f_32 / (g_f32_tflops * 1e12)) * 1e6;
@@ -1021,7 +1168,8 @@ static void roofline(Plan &P) {
 }
 
 static void plan_tiles(Plan &P) {
-  choose_layouts(P);  // first: the f32 tile form depends on B's layout
+  choose_merges(P);   // first: it rewrites the graph the other steps plan
+  choose_layouts(P);  // the f32 tile form depends on B's layout
   choose_configs(P);
   choose_fusion(P);
   choose_split(P);
@@ -1211,6 +1359,10 @@ static dag_status fill_params(const Plan &P, int v, char *const *dptr, const int
   const Graph &g = P.g;
   const dag_node_desc &n = g.nodes[v];
   memset(&q, 0, sizeof q);
+  if (merged_away(P, v)) {  // no tiles: the merged sibling computes it
+    q.tmap_a = q.tmap_b = q.tmap_c = -1;
+    return DAG_OK;
+  }
   q.A = dptr[n.a];
   q.lda = ld[n.a];
   q.a_dt = g.bufs[n.a].dtype;
@@ -1501,6 +1653,20 @@ extern "C" dag_status dag_set_output(dag_handle *h, int buf, void *host_ptr) {
 static cudaError_t copy_h2d(dag_handle *h, int b, cudaStream_t st) {
   const dag_buffer_desc &d = h->P.g.bufs[b];
   const Plan &P = h->P;
+  const int r = P.g.root[b];
+  if (r != b && P.store_t[r]) {
+    // a merged sibling's weight (K x N, batch 1): its slice of the parent kept
+    // transposed is rows [coff, coff + N) of the parent's N x K form
+    cudaError_t e = cudaSuccess;
+    if (h->staging_used) e = cudaStreamWaitEvent(st, h->ev_staging, 0);
+    if (!e) e = cudaMemcpyAsync(h->staging, h->host_in[b], (size_t)d.rows * d.cols * esize(d.dtype),
+                                cudaMemcpyHostToDevice, st);
+    char *dst = h->dptr[r] + (size_t)P.g.coff[b] * h->ld[r] * esize(d.dtype);
+    if (!e) e = launch_transpose(h->staging, d.cols, dst, h->ld[r], 1, d.rows, d.cols, esize(d.dtype), st);
+    if (!e) e = cudaEventRecord(h->ev_staging, st);
+    h->staging_used = true;
+    return e;
+  }
   if (P.store_t[b]) {  // through the staging area (one upload at a time, in any stream), then transposed
     cudaError_t e = cudaSuccess;
     if (h->staging_used) e = cudaStreamWaitEvent(st, h->ev_staging, 0);
@@ -1711,6 +1877,17 @@ extern "C" dag_status dag_get_output(dag_handle *h, int buf, void *host_ptr) {
   const int es = esize(d.dtype);
   const size_t w = (size_t)d.cols * es;
   const Plan &P = h->P;
+  const int root = P.g.root[buf];
+  if (root != buf && P.store_t[root]) {  // a merged sibling's weight: its rows of the transposed parent
+    const int64_t K = d.rows, N = d.cols;
+    std::vector<char> t((size_t)N * K * es);
+    CUDA_TRY(cudaMemcpy2D(t.data(), (size_t)K * es, h->dptr[root] + (size_t)P.g.coff[buf] * h->ld[root] * es,
+                          (size_t)h->ld[root] * es, (size_t)K * es, N, cudaMemcpyDeviceToHost));
+    char *out = static_cast<char *>(host_ptr);
+    for (int64_t n = 0; n < N; ++n)
+      for (int64_t k = 0; k < K; ++k) memcpy(out + (k * N + n) * es, t.data() + (n * K + k) * es, es);
+    return DAG_OK;
+  }
   if (P.store_t[buf]) {  // back to the caller's layout on the host
     const int64_t B = P.t_batch[buf], K = P.t_K[buf], N = P.t_N[buf];
     std::vector<char> t((size_t)B * N * K * es);
@@ -1862,10 +2039,40 @@ extern "C" dag_status dag_fusion_host(const dag_node_desc *nodes, int n_nodes, c
   if (opts) P.opt = *opts;
   dag_status s = build_graph(nodes, n_nodes, edges, n_edges, buffers, n_buffers, P.g);
   if (s) return s;
+  choose_merges(P);
   choose_layouts(P);
   choose_configs(P);
   choose_fusion(P);
   for (int v = 0; v < P.g.nn; ++v) out[v] = P.absorbed_by[v];
+  return DAG_OK;
+}
+
+static void merge_out(const Plan &P, int32_t *leader, int32_t *col_offset, int cap) {
+  for (int v = 0; v < P.g.nn && v < cap; ++v) {
+    const bool m = !P.merged_into.empty() && P.merged_into[v] >= 0;
+    if (leader) leader[v] = m ? P.merged_into[v] : -1;
+    if (col_offset) col_offset[v] = m ? P.merge_coff[v] : 0;
+  }
+}
+
+extern "C" dag_status dag_merge_get(dag_handle *h, int32_t *leader, int32_t *col_offset, int cap, int *n) {
+  dag_status s = check_handle(h);
+  if (s) return s;
+  if (!n) return fail(DAG_EINVAL, "null n");
+  *n = h->P.g.nn;
+  merge_out(h->P, leader, col_offset, cap);
+  return DAG_OK;
+}
+
+extern "C" dag_status dag_merge_host(const dag_node_desc *nodes, int n_nodes, const dag_buffer_desc *buffers,
+                                     int n_buffers, const dag_options *opts, int32_t *leader, int32_t *col_offset) {
+  if ((!leader || !col_offset) && n_nodes > 0) return fail(DAG_EINVAL, "null output array");
+  Plan P;
+  if (opts) P.opt = *opts;
+  dag_status s = build_graph(nodes, n_nodes, nullptr, 0, buffers, n_buffers, P.g);
+  if (s) return s;
+  choose_merges(P);
+  merge_out(P, leader, col_offset, n_nodes);
   return DAG_OK;
 }
 

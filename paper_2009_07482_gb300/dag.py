@@ -166,6 +166,10 @@ class Dag:
     def fusion(self):
         return abi.dag_fusion_get(self.h)
 
+    def merges(self):
+        """(leader, column offset) per kernel: sibling GEMMs the planner merged."""
+        return abi.dag_merge_get(self.h)
+
     def plan(self):
         return abi.dag_plan_get(self.h)
 

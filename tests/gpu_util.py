@@ -137,7 +137,7 @@ def compare(w, got, ref_store, bids=None):
 def check_trace(w, d):
     recs = d.trace()
     trace_check.check(w, [(r.node, r.r0, r.r1, r.c0, r.c1) for r in recs], [r.split for r in recs],
-                      [r.start_ticket for r in recs], [r.end_ticket for r in recs], d.fusion())
+                      [r.start_ticket for r in recs], [r.end_ticket for r in recs], d.fusion(), d.merges())
     return recs
 
 

@@ -170,7 +170,8 @@ def test_queue_order_is_a_legal_schedule(name, make, n_sm):
         t, info = abi.dag_plan_host(n, e, b, opts, n_sm)
         assert info.n_tiles == len(t) > 0
         start = np.arange(len(t), dtype=np.uint32) * 2
-        trace_check.check(w, t[:, :5], t[:, 5] >> 16, start, start + 1, abi.dag_fusion_host(n, e, b, opts))
+        trace_check.check(w, t[:, :5], t[:, 5] >> 16, start, start + 1, abi.dag_fusion_host(n, e, b, opts),
+                          abi.dag_merge_host(n, b, opts))
 
 
 def test_plan_algorithmic_totals():
@@ -250,6 +251,46 @@ def test_split_k_only_where_the_tile_form_runs_a_share_of_k(seed):
                     continue
                 bf16 = w.buffers[node.a].dtype == BF16
                 assert bf16 or (int(row[5]) & 0xFFFF) in (128, 256), (w.name, int(row[0]), int(row[5]) & 0xFFFF)
+
+
+def test_sibling_gemms_merge_into_one_plan_gemm():
+    """The planner merges GEMMs that read one A with private resident weights
+    (the encoder's Q/K/V projections of every head: one GEMM of 3072 columns,
+    192 tiles of 128 x 256 for 768 of 128 x 64) -- and leaves them alone under
+    merge = 1 or keep_layout = 1, with streamed weights, with outputs the
+    caller reads back, and across task components.  The plan's algorithmic
+    work is the DAG's own either way."""
+    w = encoder_block()
+    n, e, b = dagmod.describe(w, resident_inputs=True)
+    lead, off = abi.dag_merge_host(n, b, dagmod.options())
+    proj = [v for v, x in enumerate(w.nodes) if x.name.startswith("proj_")]
+    assert {lead[v] for v in proj} == {proj[0]} and sorted(off[v] for v in proj) == list(range(0, 3072, 64))
+    assert all(lead[v] < 0 for v in range(len(w.nodes)) if v not in proj)
+    t, info = abi.dag_plan_host(n, e, b, dagmod.options(), 148)
+    t1, info1 = abi.dag_plan_host(n, e, b, dagmod.options(merge=1), 148)
+    mine = t[t[:, 0] == proj[0]]
+    assert len(mine) == 192 and set((mine[:, 5] & 0xFFFF).tolist()) == {256} and mine[:, 4].max() == 3072
+    assert not any(int(r[0]) in proj[1:] for r in t)
+    assert len(t1) - len(t) == 768 - 192 and (info.flops, info.bytes) == (info1.flops, info1.bytes)
+    for o in (dagmod.options(merge=1), dagmod.options(keep_layout=1)):
+        assert all(x < 0 for x in abi.dag_merge_host(n, b, o)[0])
+    n2, _, b2 = dagmod.describe(w)  # weights streamed every submit
+    assert all(x < 0 for x in abi.dag_merge_host(n2, b2, dagmod.options())[0])
+    # three siblings per component, one of them read back by the caller
+    w3 = Workload("siblings")
+    X = w3.buf(512, 256, BF16, "input", ("uniform", 1))
+    for comp in range(2):
+        for i in range(3):
+            W = w3.buf(256, 64, BF16, "input", ("uniform", 10 + 3 * comp + i))
+            O = w3.buf(512, 64, BF16, "output" if (comp, i) == (1, 2) else "inter")
+            w3.node("gemm", X, O, b=W, component=comp)
+            if (comp, i) != (1, 2):
+                w3.node("unary", O, w3.buf(512, 64, BF16, "output"), act="relu", component=comp)
+    n3, _, b3 = dagmod.describe(w3, resident_inputs=True)
+    lead3, off3 = abi.dag_merge_host(n3, b3, dagmod.options())
+    g = [v for v, x in enumerate(w3.nodes) if x.op == "gemm"]
+    assert [lead3[v] for v in g] == [g[0], g[0], g[0], g[3], g[3], -1]
+    assert [off3[v] for v in g] == [0, 64, 128, 0, 64, 0]
 
 
 def test_no_alloc_rejects_overlapping_root_buffers():

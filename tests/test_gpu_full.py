@@ -97,6 +97,7 @@ def test_batched_random_dags_full_size():
     d.run()   # a replay of the captured graph
     recs = d.trace()
     fusion = d.fusion()
+    lead, moff = d.merges()
     rows = np.array([0, 31, 63])
     for k in (0, 1, 17, 100, 200, 255):
         w = ws[k]
@@ -106,8 +107,9 @@ def test_batched_random_dags_full_size():
         sub = [r for r in recs if noffs[k] <= r.node < noffs[k + 1]]
         tiles = np.array([(r.node - noffs[k], r.r0, r.r1, r.c0, r.c1) for r in sub], np.int32)
         fused = [h - noffs[k] if h >= 0 else -1 for h in fusion[noffs[k]:noffs[k + 1]]]
+        merged = ([h - noffs[k] if h >= 0 else -1 for h in lead[noffs[k]:noffs[k + 1]]], moff[noffs[k]:noffs[k + 1]])
         trace_check.check(w, tiles, [r.split for r in sub], [r.start_ticket for r in sub],
-                          [r.end_ticket for r in sub], fused)
+                          [r.end_ticket for r in sub], fused, merged)
     d.close()
 
 

@@ -15,7 +15,12 @@ kernel of the group on the same region.  Tickets are scaled by 8 and the
 group's tiles placed in dependency order between the tile's start and end
 tickets, the last one ending at the tile's end.  The start ticket of such a
 tile is drawn after all its waits, so every operand of the group must have
-been released before it."""
+been released before it.
+
+A tile of a merged GEMM (the library's merge map: kernel -> (the sibling
+whose tiles compute it, its first column in that GEMM's output)) covers the
+summed width of its siblings: it stands for one tile of each sibling whose
+columns it covers, on its share of them, with the same tickets."""
 import numpy as np
 
 import oracle
@@ -61,11 +66,35 @@ def expand_fused(w, tiles5, split, start, end, fused):
             np.array(en, np.uint64))
 
 
-def check(w, tiles5, split, start, end, fused=None):
+def expand_merged(w, tiles5, split, start, end, merges):
+    leader, off = merges
+    members = {}
+    for v, h in enumerate(leader):
+        if h >= 0:
+            members.setdefault(h, []).append(v)
+    T, S, st, en = [], [], [], []
+    for i, t in enumerate(np.asarray(tiles5, np.int64)):
+        node = int(t[0])
+        if node not in members:
+            T.append(t); S.append(split[i]); st.append(start[i]); en.append(end[i])
+            continue
+        for m in members[node]:
+            lo, hi = int(off[m]), int(off[m]) + w.buffers[w.nodes[m].out].cols
+            c0, c1 = max(int(t[3]), lo), min(int(t[4]), hi)
+            if c0 < c1:
+                T.append(np.array([m, t[1], t[2], c0 - lo, c1 - lo]))
+                S.append(split[i]); st.append(start[i]); en.append(end[i])
+    return (np.array(T, np.int32).reshape(-1, 5), np.array(S, np.int32), np.array(st, np.int64),
+            np.array(en, np.int64))
+
+
+def check(w, tiles5, split, start, end, fused=None, merges=None):
     tiles5 = np.asarray(tiles5, np.int32)
     split = np.asarray(split, np.int32)
     start = np.asarray(start, np.int64)
     end = np.asarray(end, np.int64)
+    if merges is not None and any(h >= 0 for h in merges[0]):
+        tiles5, split, start, end = expand_merged(w, tiles5, split, start, end, merges)
     if fused is not None and any(h >= 0 for h in fused):
         tiles5, split, start, end = expand_fused(w, tiles5, split, start, end, fused)
     assert end.max(initial=0) < 2 ** 32, "tickets out of range"
