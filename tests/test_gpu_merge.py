@@ -115,3 +115,24 @@ def test_merged_weights_read_back_and_update(dt):
     finally:
         d.close()
     compare(w, got, oracle.run(w, ins2))
+
+
+@pytest.mark.parametrize("dt", [BF16, F32])
+def test_merged_siblings_with_split_k(dt):
+    """Siblings with a long K loop on a level of few tiles: the merged GEMM
+    also splits K (bf16: 128 x 64 tiles in two partials; f32: the wide 3 x TF32
+    form over the parent weight kept K-major, in four), within the oracle's
+    tolerance and with the same bits on every submit path."""
+    w = _siblings(dt, True, "relu", [64, 64, 128], M=256, K=2048, seed=3)
+    ins = w.make_inputs()
+    d = Dag(w, options(), resident_inputs=True)
+    try:
+        tiles = d.tiles()
+    finally:
+        d.close()
+    gemm = [v for v, n in enumerate(w.nodes) if n.op == "gemm"]
+    mine = tiles[tiles[:, 0] == gemm[0]]
+    assert len(mine) == len(tiles[np.isin(tiles[:, 0], gemm)]) and ((mine[:, 5] >> 16) & 0xFF).max() >= 2
+    got, lead, _ = _run(w, ins, options(trace=1))
+    assert [lead[v] for v in gemm] == [gemm[0]] * 3
+    compare(w, got, oracle.run(w, ins))
