@@ -1679,6 +1679,8 @@ static cudaError_t copy_h2d(dag_handle *h, int b, cudaStream_t st) {
     return e;
   }
   const size_t w = (size_t)d.cols * esize(d.dtype);
+  if (h->ld[b] == d.cols)  // rows back to back on both sides: one linear copy
+    return cudaMemcpyAsync(h->dptr[b], h->host_in[b], w * d.rows, cudaMemcpyHostToDevice, st);
   return cudaMemcpy2DAsync(h->dptr[b], (size_t)h->ld[b] * esize(d.dtype), h->host_in[b], w, w, d.rows,
                            cudaMemcpyHostToDevice, st);
 }
@@ -1693,8 +1695,11 @@ static dag_status enqueue_readbacks(dag_handle *h, cudaStream_t stream) {
     }
     const dag_buffer_desc &d = h->P.g.bufs[b];
     const size_t w = (size_t)d.cols * esize(d.dtype);
-    CUDA_TRY(cudaMemcpy2DAsync(h->host_out[b], w, h->dptr[b], (size_t)h->ld[b] * esize(d.dtype), w, d.rows,
-                               cudaMemcpyDeviceToHost, h->down));
+    if (h->ld[b] == d.cols)  // rows back to back on both sides: one linear copy
+      CUDA_TRY(cudaMemcpyAsync(h->host_out[b], h->dptr[b], w * d.rows, cudaMemcpyDeviceToHost, h->down));
+    else
+      CUDA_TRY(cudaMemcpy2DAsync(h->host_out[b], w, h->dptr[b], (size_t)h->ld[b] * esize(d.dtype), w, d.rows,
+                                 cudaMemcpyDeviceToHost, h->down));
   }
   if (h->reading) CUDA_TRY(cudaEventRecord(h->ev_read, h->down));
   (void)stream;
