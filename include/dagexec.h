@@ -313,6 +313,8 @@ typedef struct {
   uint64_t timeout_ns;    /* limit on waiting for any callback; 0 = 10 s; DAG_ETIMEOUT poisons the handle */
   float *node_start_us;   /* optional [n_nodes] */
   float *node_end_us;     /* optional [n_nodes] */
+  int32_t *node_queue;    /* optional [n_nodes]: the queue setup_cq sent each kernel to (its component's
+                             kernels round-robin over n_queues in dispatch order, Alg. 1) */
 } dag_cq_options;
 
 typedef struct {

@@ -55,7 +55,8 @@ class dag_options(C.Structure):
 
 class dag_cq_options(C.Structure):
     _fields_ = [("n_queues", i32), ("components", i32), ("fifo", i32), ("pad", i32), ("timeout_ns", u64),
-                ("node_start_us", C.POINTER(f32)), ("node_end_us", C.POINTER(f32))]
+                ("node_start_us", C.POINTER(f32)), ("node_end_us", C.POINTER(f32)),
+                ("node_queue", C.POINTER(i32))]
 
 
 class dag_cq_result(C.Structure):
@@ -316,20 +317,24 @@ def dag_submit_coarse(h, stream: int = 0) -> None:
 
 
 def dag_submit_cq(h, n_queues: int = 1, components: int = 1, fifo: int = 0, timeout_ns: int = 0,
-                  n_nodes: int = 0):
+                  n_nodes: int = 0, queues: bool = False):
     """The paper's Alg. 1 on CUDA streams (synchronous).  Returns the result
-    struct and, if n_nodes > 0, per-kernel (start_us, end_us) arrays."""
+    struct and, if n_nodes > 0, per-kernel (start_us, end_us) arrays, and with
+    `queues` also the queue each kernel was sent to."""
     import numpy as np
     o = dag_cq_options(n_queues=n_queues, components=components, fifo=fifo, timeout_ns=timeout_ns)
-    ts = te = None
+    ts = te = qs = None
     if n_nodes:
         ts = np.zeros(n_nodes, np.float32)
         te = np.zeros(n_nodes, np.float32)
         o.node_start_us = ts.ctypes.data_as(C.POINTER(f32))
         o.node_end_us = te.ctypes.data_as(C.POINTER(f32))
+        if queues:
+            qs = np.full(n_nodes, -1, np.int32)
+            o.node_queue = qs.ctypes.data_as(C.POINTER(i32))
     r = dag_cq_result()
     check(lib().dag_submit_cq(h, C.byref(o), C.byref(r)), "dag_submit_cq")
-    return r, ts, te
+    return (r, ts, te, qs) if queues else (r, ts, te)
 
 
 def dag_wait(h, timeout_ns: int = 30_000_000_000) -> int:

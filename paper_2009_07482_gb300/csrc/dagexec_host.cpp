@@ -2299,8 +2299,8 @@ extern "C" dag_status dag_submit_cq(dag_handle *h, const dag_cq_options *o, dag_
   for (int b = 0; b < g.nb; ++b) writers_left[b] = (int)writers[b].size();
   std::vector<int> qof(n, -1), order;  // order: components in dispatch order
   std::vector<char> processed(n, 0);
-  int rr = 0;
   auto setup_cq = [&](int c) -> cudaError_t {
+    int rr = 0;  // init(): each component's queue structure selects from q_0 on (sel_rr)
     std::vector<int> unprocessed;
     for (int v : members[c])
       if (front[v]) unprocessed.push_back(v);
@@ -2429,6 +2429,7 @@ extern "C" dag_status dag_submit_cq(dag_handle *h, const dag_cq_options *o, dag_
     dev = std::max(dev, (double)t_end[v]);
     if (o->node_start_us) o->node_start_us[v] = t_beg[v];
     if (o->node_end_us) o->node_end_us[v] = t_end[v];
+    if (o->node_queue) o->node_queue[v] = qof[v];
   }
   double gap = 0.0;
   for (size_t i = 1; i < order.size(); ++i) {

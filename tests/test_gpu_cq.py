@@ -155,3 +155,38 @@ def test_spec_files_run_on_both_executors(name, sym):
     assert r.n_components == len(set(n.component for n in sd.nodes))
     assert bits_equal(base, _outputs(d, w))
     d.close()
+
+
+def test_setup_cq_follows_the_papers_worked_example():
+    """The paper's DAG of §3 (component T = {k0..k4}, fed by {k5, k6} and
+    feeding {k7, k8}) with three command queues: setup_cq sends k0..k4 to
+    q0, q1, q2, q0, q1 (§4.B, its example of Fig. 'dispatch'; round-robin over
+    the component's own queues, in dispatch order), and the results match the
+    oracle and the persistent executor bit for bit."""
+    from tests.conftest import load_golden
+    g = load_golden("paper_fig_platform_dag.json")
+    w = Workload("paper_platform_dag")
+    bid = {}
+    sinks = {"y7", "y8"}
+    for i, nme in enumerate(g["buffers"]):
+        role = "input" if nme in g["inputs"] else "output" if nme in sinks else "inter"
+        bid[nme] = w.buf(192, 256, F32, role, ("uniform", 300 + i) if role == "input" else None, nme)
+    kid = {}
+    for k, spec in g["kernels"].items():
+        kw = {"b": bid[spec["b"]]} if "b" in spec else {"act": "relu"}
+        kid[k] = w.node(spec["op"], bid[spec["a"]], bid[spec["out"]], name=k, component=spec["component"], **kw)
+    ins = w.make_inputs()
+    d = Dag(w, options(), resident_inputs=False)
+    try:
+        d.set_inputs(ins)
+        d.run()
+        fine = _outputs(d, w)
+        r, _, _, q = abi.dag_submit_cq(d.h, n_queues=g["setup_cq"]["n_queues"], components=abi.DAG_TC_GIVEN,
+                                       n_nodes=len(w.nodes), queues=True)
+        assert r.n_components == 3
+        cq = _outputs(d, w)
+    finally:
+        d.close()
+    assert {k: int(q[kid[k]]) for k in g["setup_cq"]["queue"]} == g["setup_cq"]["queue"]
+    compare(w, fine, oracle.run(w, ins))
+    assert bits_equal(fine, cq)
