@@ -123,6 +123,19 @@ def run_timeline(args, w, d, abi, stream, flush, reps=8):
             "kernels": out}
 
 
+def e2e_chunks(wl, n):
+    """The batch in n consecutive shares of DAGs, for the end-to-end path's
+    back-to-back launches: [(DAGs, {buffer id in concat(wl): id in concat(DAGs)})]."""
+    per = -(-len(wl) // n)
+    out, goff = [], 0
+    for c in range(0, len(wl), per):
+        part = wl[c:c + per]
+        nbuf = sum(len(x.buffers) for x in part)
+        out.append((part, {g: g - goff for g in range(goff, goff + nbuf)}))
+        goff += nbuf
+    return out
+
+
 def make_workload(name, n_dags=256):
     """(workload, description); for "batched" the workload is the list of DAGs."""
     from synth.workloads import branchy_mlp, encoder_block, fork_join, random_batch
@@ -1138,16 +1151,10 @@ def main():
     d.close()
     e2e_parts = []  # (handle, {global buffer id: local id})
     if batched:
-        per = -(-len(wl) // E2E_CHUNKS)
-        goff = 0
-        for c in range(0, len(wl), per):
-            part = wl[c:c + per]
-            nbuf = sum(len(x.buffers) for x in part)
-            loc = {g: g - goff for g in range(goff, goff + nbuf)}
+        for part, loc in e2e_chunks(wl, E2E_CHUNKS):
             o = options(use_graph=1, f32_gemm=abi.DAG_F32_GEMM_SIMT if args.f32_simt else 0)
             eh = Dag.batch(part, o, resident_inputs=False, streamed={loc[i] for i in X_ids if i in loc})
             e2e_parts.append((eh, loc))
-            goff += nbuf
     else:
         e2e_parts.append((make_dag(True), {i: i for i in range(len(w.buffers))}))
     pins = []

@@ -1,5 +1,8 @@
 """bench.py's all-cores oracle baseline: spawned processes, each timing the
-oracle on its own batch rows at the same moment (CPU only, two processes)."""
+oracle on its own batch rows at the same moment (CPU only, two processes);
+and the end-to-end path's split of the batch into back-to-back launches."""
+import pytest
+
 import bench
 
 
@@ -46,3 +49,24 @@ def test_reference_arm_times_whole_units():
     assert f2 == f                       # step 32 wraps to DAGs 0..7
     units, f, _ = bench.reference_units("encoder", 0)
     assert f == 1 / 8 and len(units) == 1
+
+
+@pytest.mark.parametrize("n_dags,n", [(256, 8), (13, 4), (3, 8)])
+def test_end_to_end_chunks_cover_the_batch_once(n_dags, n):
+    """The end-to-end path's shares of the batch: consecutive, every DAG in
+    one share, and each share's buffer ids those of concat(share) shifted
+    from concat(batch) -- so inputs, streamed activations and sinks land on
+    the handle that owns them."""
+    from synth.workloads import concat, random_batch
+    wl = random_batch(n_dags)
+    chunks = bench.e2e_chunks(wl, n)
+    assert len(chunks) <= n and [x for part, _ in chunks for x in part] == wl
+    whole = concat(wl)
+    seen = set()
+    for part, loc in chunks:
+        local = concat(part)
+        assert sorted(loc.values()) == list(range(len(local.buffers)))
+        for g, l in loc.items():
+            assert whole.buffers[g] == local.buffers[l]
+        seen |= set(loc)
+    assert seen == set(range(len(whole.buffers)))
