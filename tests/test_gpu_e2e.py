@@ -121,3 +121,58 @@ def test_registered_readback_full_size_mlp(dt):
             assert e <= node_tolerance(w, Y), f"sink {Y}: rel err {e:.3e}"
     for Y, g in runs[-1][1].items():
         assert np.array_equal(g.view(np.uint8), dev[Y].view(np.uint8))
+
+
+def test_back_to_back_batch_launches_read_back_their_own_sinks():
+    """The end-to-end path's form for a batch: shares of the DAGs on separate
+    handles, submitted back to back on one stream with streamed activations
+    and registered readbacks, each launch's readback overlapping the next
+    launch.  Every sink of every DAG equals the oracle on its inputs and, bit
+    for bit, what dag_get_output reads from its handle afterwards."""
+    import bench
+    from synth.workloads import concat, random_batch
+    wl = random_batch(12, base_seed=1300, max_nodes=24, sizes=(64, 128, 256, 512))
+    parts = []
+    try:
+        for part, _ in bench.e2e_chunks(wl, 3):
+            w = concat(part)
+            X_ids = activation_ids(w)
+            d = Dag.batch(part, options(use_graph=1), resident_inputs=False, streamed=set(X_ids))
+            base = w.make_inputs()
+            d.set_inputs({k: v for k, v in base.items() if k not in X_ids})
+            d.run()
+            pins = {}
+            for i in X_ids:
+                b = w.buffers[i]
+                p = abi.dag_host_alloc(b.rows * b.cols * (4 if b.dtype == "f32" else 2))
+                v = _pinned_view(p, b)
+                v[:] = synth.fill("uniform", 90_000 + i, (b.rows, b.cols), b.dtype, -1.0, 1.0)
+                base[i] = v.copy()
+                abi.dag_set_input(d.h, i, p)
+                pins[i] = p
+            outs = {}
+            for Y in w.output_ids():
+                b = w.buffers[Y]
+                p = abi.dag_host_alloc(b.rows * b.cols * (4 if b.dtype == "f32" else 2))
+                outs[Y] = (p, _pinned_view(p, b))
+                abi.dag_set_output(d.h, Y, p)
+            parts.append((w, d, base, pins, outs))
+        for _ in range(2):
+            for _, d, _, _, _ in parts:
+                d.submit()
+            for _, d, _, _, _ in parts:
+                abi.check(d.wait(), "dag_wait")
+        for w, d, base, _, outs in parts:
+            ref = oracle.run(w, base)
+            for Y, (_, v) in outs.items():
+                dt = w.buffers[Y].dtype
+                e = oracle.rel_err(storage_to_f64(v.copy(), dt), storage_to_f64(oracle.view(w, ref, Y), dt))
+                assert e <= node_tolerance(w, Y), f"{w.name} sink {Y}: rel err {e:.3e}"
+                assert np.array_equal(v.view(np.uint8), d.output(Y).view(np.uint8)), f"sink {Y}: readback != device"
+    finally:
+        for w, d, _, pins, outs in parts:
+            for Y in outs:
+                abi.dag_set_output(d.h, Y, None)
+            d.close()
+            for p in list(pins.values()) + [p for p, _ in outs.values()]:
+                abi.dag_host_free(p)
