@@ -173,7 +173,7 @@ def make_workload(name, n_dags=256):
                    "larger than L2 together (memory-bound)")
     if name == "heads":
         from synth.workloads import transformer_heads
-        return transformer_heads(16, 256), ("the paper's transformer-layer DAG (§6): 16 heads, beta = 256, f32; "
+        return transformer_heads(16, 256), ("the paper's transformer-layer DAG (§5): 16 heads, beta = 256, f32; "
                                             "per head 3 projections, Q.K^T, softmax, B.V, C.W_h")
     return encoder_block(), ("transformer encoder block DAG: 8 x 256 tokens, d_model 1024, 16 heads as fork "
                              "branches, out proj, FFN 4096 GELU; bf16 in / f32 accumulate")
@@ -278,7 +278,7 @@ def run_exp1(args):
             rows23.append(row)
             d.close()
     last = rows[-1]
-    line = {"metric": "DAG makespan (us), paper §6 Experiment 1 transformer DAGs (beta 256, f32)",
+    line = {"metric": "DAG makespan (us), paper §5 Experiment 1 transformer DAGs (beta 256, f32)",
             "value": last["persistent_us"], "unit": "us", "higher_is_better": False, "n_gpus": 1,
             "dtype": "f32", "data": "synthetic (seeded SplitMix64)",
             "config": {"workload": "transformer_heads H in {1,2,4,8,16}, beta 256; value = persistent executor at H=16",

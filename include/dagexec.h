@@ -223,7 +223,10 @@ dag_status dag_create(const dag_node_desc *nodes, int n_nodes, const dag_edge *e
  * work queue, so small and large DAGs fill the GPU together).  Buffer ids of
  * item i in the returned handle are offset by the buffer counts of items
  * 0..i-1; node ids likewise by their node counts.  Everything else is as for
- * dag_create (opts applies to the whole batch).
+ * dag_create (opts applies to the whole batch).  The paper's DAG G of §3 may
+ * already consist of several independent task components (the H heads of
+ * §5's Experiment 1 are one DAG); a batch is such a G built from separate
+ * descriptions.
  */
 typedef struct {
   const dag_node_desc *nodes;
@@ -269,7 +272,7 @@ dag_status dag_submit(dag_handle *h, void *stream);
 
 /* dag_submit_coarse: the coarse-grained baseline (§2, one command queue: each
  * kernel's write, ndrange and read commands finish before the next kernel's;
- * §6's default configuration): uploads on `stream`, then one launch per kernel
+ * §5's default configuration): uploads on `stream`, then one launch per kernel
  * in topological order on `stream` (the same tile code, a grid of that
  * kernel's tiles, no cross-kernel overlap), then readbacks.
  * A GEMM with fused elementwise kernels launches in the place of the last of
@@ -277,8 +280,9 @@ dag_status dag_submit(dag_handle *h, void *stream);
 dag_status dag_submit_coarse(dag_handle *h, void *stream);
 
 /*
- * dag_submit_cq: the paper's own fine-grained form (§5, Alg. 1) on CUDA
- * streams, as a second, host-driven executor over the same tiles:
+ * dag_submit_cq: the paper's own fine-grained form (§4.B, Alg. 1; the
+ * clustering scheme of §5) on CUDA streams, as a second, host-driven executor
+ * over the same tiles:
  *   schedule: ready task components (every kernel of FRONT(T) has all its
  *     predecessors finished) wait in a priority queue F ordered by the largest
  *     bottom-level rank of their FRONT kernels (or by id with fifo = 1); the
@@ -298,7 +302,7 @@ dag_status dag_submit_coarse(dag_handle *h, void *stream);
  * Components: DAG_TC_GIVEN uses dag_node_desc.component (the partition must
  * leave the component graph acyclic, else DAG_ECYCLE); DAG_TC_WHOLE puts the
  * DAG in one component; DAG_TC_PER_KERNEL makes every kernel a component
- * (the coarse-grained policies of §6, Experiments 2-3: one callback per
+ * (the coarse-grained policies of §5, Experiments 2-3: one callback per
  * kernel).  Timings come from CUDA events on the streams; node_start_us /
  * node_end_us, if not NULL, receive each kernel's [start, end) from the first
  * dispatch (n_nodes entries each, caller-owned).
@@ -335,7 +339,8 @@ dag_status dag_submit_cq(dag_handle *h, const dag_cq_options *opts, dag_cq_resul
  * (the handle is poisoned), DAG_EDEVICE on a CUDA error. */
 dag_status dag_wait(dag_handle *h, uint64_t timeout_ns);
 
-/* dag_poll: non-blocking dag_wait: DAG_EBUSY while the last submit (with its
+/* dag_poll: non-blocking dag_wait (Alg. 1's sleep_till_cb_update of §4.B
+ * asked once instead of waited on): DAG_EBUSY while the last submit (with its
  * readbacks) is still running, else what dag_wait would return. */
 dag_status dag_poll(dag_handle *h);
 
@@ -358,16 +363,22 @@ const void *dag_device_ptr(dag_handle *h, int buf, int64_t *ld_elems);
  * objects of §4.B; NULL is accepted (DAG_OK). */
 dag_status dag_destroy(dag_handle *h);
 
-/* dag_last_error: message of the last failure on this thread ("" if none). */
+/* dag_last_error: message of the last failure on this thread ("" if none).
+ * Library plumbing with no counterpart in the paper. */
 const char *dag_last_error(void);
 
 /* dag_set_device: make CUDA device `ordinal` current for the calling host
  * thread inside the library (the library links its own CUDA runtime, so a
  * device chosen through another runtime instance does not carry over).
- * Handles created afterwards on this thread live on that device. */
+ * Handles created afterwards on this thread live on that device.  The paper's
+ * device set A (§4.B) has one GPU here; this picks which. */
 dag_status dag_set_device(int ordinal);
 
-/* pinned host memory for asynchronous uploads/readbacks */
+/* pinned host memory for asynchronous uploads/readbacks: the host side of the
+ * isolated writes and reads of §3 (dag_set_input / dag_set_output), so that
+ * they run on the copy engines beside the launch.  NULL on failure
+ * (dag_last_error says why);
+ * dag_host_free(NULL) is a no-op. */
 void *dag_host_alloc(size_t bytes);
 void dag_host_free(void *p);
 
@@ -417,6 +428,9 @@ dag_status dag_run_noalloc(const dag_node_desc *nodes, int n_nodes, const dag_bu
  * admitted request launches immediately, so requests arriving while others
  * run overlap them on the device.  node_cost_us (may be NULL) gives the
  * per-kernel costs that rank each slot's queue (learned or measured).
+ * No counterpart in the paper, which runs one DAG at a time: each request is
+ * one persistent launch of its slot's plan (dag_submit, a valid schedule in
+ * the sense of Def. 5, ordered by §5's bottom-level ranks).
  */
 typedef struct {
   const dag_node_desc *nodes;
@@ -543,7 +557,9 @@ typedef struct {
 } dag_trace_record;
 
 /* dag_trace_get: records of the last submit in queue order (needs
- * opts.trace; call after dag_wait); *n = number of tiles. */
+ * opts.trace; call after dag_wait); *n = number of tiles.  The data of the
+ * paper's Gantt charts (§2, §5) at tile granularity; the tickets let a checker
+ * confirm that the run was a valid schedule (Def. 5). */
 dag_status dag_trace_get(dag_handle *h, dag_trace_record *out, int cap, int *n);
 
 /* dag_trace_stamps: per tile (queue order of the last submit), ten
@@ -557,11 +573,12 @@ dag_status dag_trace_stamps(dag_handle *h, uint64_t *out, int cap, int *n);
  * dag_options.trace): enter_exit[0] = the earliest CTA entry, enter_exit[1] =
  * the latest CTA exit, on the %globaltimer clock (ns) of dag_trace_stamps, so
  * that the executor's own start-up and tear-down show beside the tiles' phases
- * (the launch's part of the paper's Gantt charts, §2 and §6).  DAG_EINVAL if
+ * (the launch's part of the paper's Gantt charts, §2 and §5).  DAG_EINVAL if
  * tracing is off or the last submit was not a persistent launch. */
 dag_status dag_trace_launch(dag_handle *h, uint64_t *enter_exit);
 
-/* Static plan facts. */
+/* Static plan facts (no counterpart in the paper; critical_path_us is the
+ * largest bottom-level rank of §5 under the roofline time model). */
 typedef struct {
   int32_t n_tiles, n_counters, n_waits, grid;
   int32_t smem_bytes;
@@ -581,17 +598,22 @@ dag_status dag_plan_get(dag_handle *h, dag_plan_info *out);
  * if v keeps its own tiles) and col_offset[v] = its first column in the
  * merged GEMM's output (0 if not merged).  The merged kernel's tiles (its id
  * in dag_tiles_get and the trace) cover the summed width.  cap entries at
- * most; *n = kernel count.  dag_merge_host: the same without a device. */
+ * most; *n = kernel count.  dag_merge_host: the same without a device.  Not
+ * in the paper: a planning step below its kernels, which still run in a
+ * topological order of G (Def. 5). */
 dag_status dag_merge_get(dag_handle *h, int32_t *leader, int32_t *col_offset, int cap, int *n);
 dag_status dag_merge_host(const dag_node_desc *nodes, int n_nodes, const dag_buffer_desc *buffers, int n_buffers,
                           const dag_options *opts, int32_t *leader, int32_t *col_offset);
 
 /* Per-kernel costs (us) the plan's ranks were computed from: the roofline
- * time model's, or node_cost_us as given; n = kernel count. */
+ * time model's, or node_cost_us as given; n = kernel count.  These are the
+ * kernel times behind §5's bottom-level ranks (HEFT's profiled times). */
 dag_status dag_node_costs_get(dag_handle *h, float *out, int cap, int *n);
 
 /* Per-tile static description in queue order: {node, r0, r1, c0, c1,
- * cfg | split << 16} (cfg: the tile shape code; split as in dag_trace_record). */
+ * cfg | split << 16} (cfg: the tile shape code; split as in dag_trace_record).
+ * A tile is this library's unit of fine-grained dispatch: the role the work
+ * groups of concurrently dispatched kernels play in §2. */
 dag_status dag_tiles_get(dag_handle *h, int32_t *out6, int cap, int *n);
 
 /* Epilogue fusion of the plan (see dag_options.fuse): out[v] = the GEMM

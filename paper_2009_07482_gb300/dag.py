@@ -137,7 +137,7 @@ class Dag:
                               fifo: int = 0):
         """Run the paper's Alg. 1 on streams (run_cq) and write each kernel's
         window as a Chrome trace-event file, one process per task component
-        (the Gantt view of the paper's §6).  Returns the dag_cq_result."""
+        (the Gantt view of the paper's §5).  Returns the dag_cq_result."""
         import json
         from .trace import kernel_windows_trace
         r, ts, te = self.run_cq(n_queues=n_queues, components=components, fifo=fifo, times=True)

@@ -1,7 +1,7 @@
 """Chrome trace-event export of an executor launch (a Gantt chart per SM).
 
 The paper reads its schedules off Gantt charts of OpenCL command timings
-(write / ndrange / read per queue, §2 and §6).  Here the unit of work is a
+(write / ndrange / read per queue, §2 and §5).  Here the unit of work is a
 tile, and the executor's trace (dag_trace_get, with dag_options.trace = 1)
 records for each tile the SM it ran on and four %globaltimer times: the claim
 of its queue position, the end of its dependency waits, the moment the worker
@@ -74,7 +74,7 @@ def write_chrome_trace(path: str, records: Sequence, names: Optional[Sequence[st
 def kernel_windows_trace(start_us: Sequence[float], end_us: Sequence[float], names: Sequence[str],
                          groups: Optional[Sequence[int]] = None, group_label: str = "component") -> Dict:
     """Trace-event JSON of whole-kernel windows, as the paper's Gantt charts of
-    its schedules (§6): e.g. the [start, end) of each kernel under the paper's
+    its schedules (§5): e.g. the [start, end) of each kernel under the paper's
     Alg. 1 on streams (dag_submit_cq with per-kernel times).  One process per
     group (task component); inside it, kernels are packed in start order onto
     the first lane free at their start, so a lane never holds two kernels at

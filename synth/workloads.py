@@ -275,7 +275,7 @@ def encoder_block(batch: int = 8, seq: int = 256, d_model: int = 1024, heads: in
 
 def transformer_heads(heads: int = 16, beta: int = 256, dtype: str = F32, seed: int = 4,
                       softmax_scale: float = 1.0) -> Workload:
-    """The paper's transformer-layer DAG of §6 (its Experiments 1-3): every
+    """The paper's transformer-layer DAG of §5 (its Experiments 1-3): every
     matrix beta x beta; per head h: Q=X.Wq, K=X.Wk, V=X.Wv, A=Q.K^T (K read
     as a K-major operand: the transpose kernel is fused away), B=softmax(A),
     C=B.V, Z[:, h] = C.Wh (heads concatenated in place).  Each head is one

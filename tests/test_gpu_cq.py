@@ -1,7 +1,7 @@
-"""The paper's own fine-grained form (§5, Alg. 1) on CUDA streams
-(dag_submit_cq): the same tiles as the persistent executor, so the same bits;
-dependency-legal kernel times; one component at a time on the device; the
-callback count the component partition implies."""
+"""The paper's own fine-grained form (§4.B, Alg. 1; the clustering scheme of
+§5) on CUDA streams (dag_submit_cq): the same tiles as the persistent
+executor, so the same bits; dependency-legal kernel times; one component at a
+time on the device; the callback count the component partition implies."""
 import numpy as np
 import pytest
 
@@ -88,7 +88,7 @@ def test_cq_same_bits_as_persistent_and_legal_times(name, make):
 
 
 def test_cq_heads_one_component_at_a_time():
-    """The clustering partition of §6 (one task component per head): heads
+    """The clustering partition of §5 (one task component per head): heads
     run one after another on the one device, each over its own queues."""
     H = 4
     w = transformer_heads(H, 128)
