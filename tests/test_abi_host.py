@@ -293,6 +293,38 @@ def test_sibling_gemms_merge_into_one_plan_gemm():
     assert [off3[v] for v in g] == [0, 64, 128, 0, 64, 0]
 
 
+def test_trace_checker_sees_a_merged_tile_as_its_siblings_shares():
+    """A merged GEMM's tile stands for its siblings' shares of its columns:
+    the queue order passes only with the merge map given (without it the
+    siblings' regions are never written); a tile reading a projection that
+    starts before the merged tiles holding its columns have ended fails, and
+    so does a trace missing one merged tile."""
+    w = encoder_block(batch=2, seq=64, d_model=128, heads=4, d_head=32, ffn=256)
+    n, e, b = dagmod.describe(w, resident_inputs=True)
+    opts = dagmod.options()
+    t, _ = abi.dag_plan_host(n, e, b, opts, 148)
+    fused, merges = abi.dag_fusion_host(n, e, b, opts), abi.dag_merge_host(n, b, opts)
+    proj = [v for v, x in enumerate(w.nodes) if x.name.startswith("proj_")]
+    L = merges[0][proj[0]]
+    assert L >= 0 and all(merges[0][v] == L for v in proj)
+    start = np.arange(len(t), dtype=np.int64) * 2 + 2
+    args = (t[:, :5], t[:, 5] >> 16)
+    trace_check.check(w, *args, start, start + 1, fused, merges)
+    with pytest.raises(AssertionError, match="illegal trace"):
+        trace_check.check(w, *args, start, start + 1, fused, None)
+    outs = {w.nodes[v].out for v in proj}
+    readers = {v for v, x in enumerate(w.nodes) if x.op == "gemm" and ({x.a, x.b} & outs) and v not in proj}
+    c = next(i for i, r in enumerate(t) if int(r[0]) in readers)
+    early = start.copy()
+    early[c] = 0                   # before every merged projection tile has ended
+    with pytest.raises(AssertionError, match="illegal trace"):
+        trace_check.check(w, *args, early, start + 1, fused, merges)
+    keep = np.ones(len(t), bool)
+    keep[np.nonzero(t[:, 0] == L)[0][0]] = False
+    with pytest.raises(AssertionError, match="illegal trace"):
+        trace_check.check(w, t[keep, :5], t[keep, 5] >> 16, start[keep], start[keep] + 1, fused, merges)
+
+
 def test_no_alloc_rejects_overlapping_root_buffers():
     """dag_run_noalloc: two root buffers sharing device memory (an output
     placed on an input, or rows of one falling inside another) are rejected
