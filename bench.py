@@ -66,6 +66,9 @@ def parse():
                     help="batched: number of DAGs (256 = the configuration; fewer only for profiling captures)")
     ap.add_argument("--profile", action="store_true", help="few steps, no side measurements (for ncu)")
     ap.add_argument("--f32-simt", action="store_true", help="f32 GEMMs on the SM cores (FFMA) instead of 3 x TF32")
+    ap.add_argument("--tile-override", type=int, default=0, choices=[0, 64, 128, 256],
+                    help="diagnostic: force the tensor-core GEMM tile width (dag_options.tile_override; "
+                         "0 = the planner's choice)")
     ap.add_argument("--timeline", action="store_true",
                     help="diagnostic: per-kernel phases of traced launches (claim, dependencies, K loop, epilogue, "
                          "release) instead of the measured line")
@@ -1045,7 +1048,7 @@ def main():
 
     def make_dag(streamed, fuse=0, trace=0, merge=0):
         o = options(use_graph=1 if batched else 0, f32_gemm=abi.DAG_F32_GEMM_SIMT if args.f32_simt else 0,
-                    fuse=fuse, trace=trace, merge=merge)
+                    fuse=fuse, trace=trace, merge=merge, tile_override=args.tile_override)
         if batched:
             return Dag.batch(wl, o, resident_inputs=not streamed, streamed=set(X_ids) if streamed else None)
         return Dag(w, o, streamed=set(X_ids)) if streamed else Dag(w, o, resident_inputs=True)
@@ -1215,6 +1218,7 @@ def main():
                    "grid": info.grid,
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "f32_gemm": "SM cores (FFMA)" if args.f32_simt else "tensor cores (3 x TF32 split)",
+                   **({"tile_override": args.tile_override} if args.tile_override else {}),
                    "parallelism": f"replicas x{world} (independent DAGs per GPU)" if world > 1 else "1 GPU"},
         "makespan_us": {"median": med, "p10": float(q[0]), "p90": float(q[1]), "mean": statistics.mean(fine_us)},
         "coarse": {"median_us": cmed, "launches_per_step": n_coarse_launches,
