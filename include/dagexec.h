@@ -354,7 +354,9 @@ dag_status dag_get_output(dag_handle *h, int buf, void *host_ptr);
 
 /* dag_device_ptr: device address of buffer `buf` (borrowed, valid until
  * dag_destroy) and its row pitch in elements; NULL on a bad id and for a
- * weight kept transposed on the device (dag_options.keep_layout). */
+ * weight kept transposed on the device (dag_options.keep_layout).  The
+ * device-side buffer b of §3's B, for callers that chain their own kernels;
+ * the paper's OpenCL buffers have no such accessor. */
 const void *dag_device_ptr(dag_handle *h, int buf, int64_t *ld_elems);
 
 /* dag_destroy: wait for outstanding work (bounded), free everything the
@@ -565,8 +567,11 @@ dag_status dag_trace_get(dag_handle *h, dag_trace_record *out, int cap, int *n);
 /* dag_trace_stamps: per tile (queue order of the last submit), ten
  * %globaltimer stamps (ns): claim, dependencies satisfied, last operand load
  * issued, first MMA, last MMA committed, workers start, accumulator ready,
- * stores issued, fence and barrier done, release done (0 where a phase does
- * not apply).  out holds 10 * cap values.  Diagnostic; needs opts.trace. */
+ * body done (the first worker warp's part: its stores issued, or completed
+ * where they are TMA stores), fence and barrier done, release done (0 where
+ * a phase does not apply).  out holds 10 * cap values.  Diagnostic; needs
+ * opts.trace.  The phases inside each bar of the paper's Gantt charts (§2,
+ * §5), per tile. */
 dag_status dag_trace_stamps(dag_handle *h, uint64_t *out, int cap, int *n);
 
 /* dag_trace_launch: the window of the last persistent launch traced (needs
@@ -620,7 +625,9 @@ dag_status dag_tiles_get(dag_handle *h, int32_t *out6, int cap, int *n);
  * kernel whose tiles compute kernel v, or -1 when v runs its own tiles;
  * n = kernel count.  A fused kernel's buffer between the GEMM and it is never
  * written; the GEMM's tiles write the last fused kernel's output, and their
- * trace records carry the GEMM's id. */
+ * trace records carry the GEMM's id.  Not in the paper: the fused kernels
+ * still finish in a topological order of G (Def. 5), their tiles with the
+ * GEMM's. */
 dag_status dag_fusion_get(dag_handle *h, int32_t *out, int cap, int *n);
 
 /* Host-only: the fusion dag_create would choose (as dag_fusion_get), n_nodes
@@ -630,12 +637,15 @@ dag_status dag_fusion_host(const dag_node_desc *nodes, int n_nodes, const dag_ed
 
 /* Host-only planning, no device needed: the tiles in queue order (as
  * dag_tiles_get) that dag_create would build for a GPU with n_sm SMs running
- * one executor CTA per SM.  info may be NULL. */
+ * one executor CTA per SM.  info may be NULL.  The queue is a topological
+ * order of the tile graph, the tile-level form of Def. 5's dispatch order. */
 dag_status dag_plan_host(const dag_node_desc *nodes, int n_nodes, const dag_edge *edges, int n_edges,
                          const dag_buffer_desc *buffers, int n_buffers, const dag_options *opts, int n_sm,
                          int32_t *out6, int cap, int *n_tiles, dag_plan_info *info);
 
-/* Peaks used by the roofline estimates and the time model (TFLOP/s, GB/s). */
+/* Peaks used by the roofline estimates and the time model (TFLOP/s, GB/s),
+ * the time model behind §5's bottom-level ranks when no measured or learned
+ * kernel times are given. */
 void dag_set_peaks(double bf16_tflops, double f32_tflops, double hbm_gbs);
 
 #ifdef __cplusplus
