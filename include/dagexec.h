@@ -603,7 +603,9 @@ dag_status dag_plan_get(dag_handle *h, dag_plan_info *out);
  * if v keeps its own tiles) and col_offset[v] = its first column in the
  * merged GEMM's output (0 if not merged).  The merged kernel's tiles (its id
  * in dag_tiles_get and the trace) cover the summed width.  cap entries at
- * most; *n = kernel count.  dag_merge_host: the same without a device.  Not
+ * most; *n = kernel count.  The parent buffers are internal: the buffer
+ * calls reject their ids with DAG_EINVAL, as any id the caller did not
+ * describe.  dag_merge_host: the same without a device.  Not
  * in the paper: a planning step below its kernels, which still run in a
  * topological order of G (Def. 5). */
 dag_status dag_merge_get(dag_handle *h, int32_t *leader, int32_t *col_offset, int cap, int *n);

@@ -465,6 +465,12 @@ static inline bool merged_away(const Plan &P, int v) {
 // kept per root row block, see the views as they see every view.  The
 // merged GEMM inherits the successors of all its siblings (Alg. 1's task
 // components keep their order), and the siblings keep no tiles of their own.
+// A buffer id of the caller's description (not a parent the planner added
+// for merged siblings): the only ids the public calls accept.
+static bool caller_buf(const Plan &P, int b) {
+  return b >= 0 && b < P.g.nb && !(b < (int)P.merge_parent.size() && P.merge_parent[b]);
+}
+
 static void choose_merges(Plan &P) {
   if (P.merged_done) return;
   P.merged_done = true;
@@ -1631,7 +1637,7 @@ static dag_status check_handle(dag_handle *h) {
 extern "C" dag_status dag_set_input(dag_handle *h, int buf, const void *host_ptr) {
   dag_status s = check_handle(h);
   if (s) return s;
-  if (buf < 0 || buf >= h->P.g.nb || !(h->P.g.bufs[buf].flags & DAG_BUF_INPUT))
+  if (!caller_buf(h->P, buf) || !(h->P.g.bufs[buf].flags & DAG_BUF_INPUT))
     return fail(DAG_EINVAL, "buffer %d is not an input", buf);
   if (h->in_flight) return fail(DAG_EBUSY, "a submit is in flight");
   h->host_in[buf] = host_ptr;
@@ -1642,7 +1648,7 @@ extern "C" dag_status dag_set_input(dag_handle *h, int buf, const void *host_ptr
 extern "C" dag_status dag_set_output(dag_handle *h, int buf, void *host_ptr) {
   dag_status s = check_handle(h);
   if (s) return s;
-  if (buf < 0 || buf >= h->P.g.nb) return fail(DAG_EINVAL, "bad buffer %d", buf);
+  if (!caller_buf(h->P, buf)) return fail(DAG_EINVAL, "bad buffer %d", buf);
   if (h->P.store_t[h->P.g.root[buf]])
     return fail(DAG_EINVAL, "buffer %d is a weight kept transposed on the device: read it with dag_get_output", buf);
   if (h->in_flight) return fail(DAG_EBUSY, "a submit is in flight");
@@ -1876,7 +1882,7 @@ extern "C" dag_status dag_poll(dag_handle *h) {
 extern "C" dag_status dag_get_output(dag_handle *h, int buf, void *host_ptr) {
   dag_status s = check_handle(h);
   if (s) return s;
-  if (buf < 0 || buf >= h->P.g.nb || !host_ptr) return fail(DAG_EINVAL, "bad buffer or pointer");
+  if (!caller_buf(h->P, buf) || !host_ptr) return fail(DAG_EINVAL, "bad buffer or pointer");
   if (h->in_flight) return fail(DAG_EBUSY, "call dag_wait first");
   const dag_buffer_desc &d = h->P.g.bufs[buf];
   const int es = esize(d.dtype);
@@ -1910,7 +1916,7 @@ extern "C" dag_status dag_get_output(dag_handle *h, int buf, void *host_ptr) {
 }
 
 extern "C" const void *dag_device_ptr(dag_handle *h, int buf, int64_t *ld_elems) {
-  if (!h || buf < 0 || buf >= h->P.g.nb || h->P.store_t[h->P.g.root[buf]]) return nullptr;
+  if (!h || !caller_buf(h->P, buf) || h->P.store_t[h->P.g.root[buf]]) return nullptr;
   if (ld_elems) *ld_elems = h->ld[buf];
   return h->dptr[buf];
 }

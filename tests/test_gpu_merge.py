@@ -136,3 +136,27 @@ def test_merged_siblings_with_split_k(dt):
     got, lead, _ = _run(w, ins, options(trace=1))
     assert [lead[v] for v in gemm] == [gemm[0]] * 3
     compare(w, got, oracle.run(w, ins))
+
+
+def test_merge_parents_are_not_caller_buffers():
+    """The parent buffers the planner adds for a merged group are internal:
+    every buffer call rejects their ids as it rejects any id the caller did
+    not describe, while the siblings' own buffers stay addressable."""
+    w = _siblings(BF16, True, "relu", [64, 64, 128], seed=7)
+    d = Dag(w, options(), resident_inputs=True)
+    host = np.zeros(1 << 20, np.uint8)
+    try:
+        assert any(h >= 0 for h in d.merges()[0])
+        nb = len(w.buffers)
+        for bad in (nb, nb + 1, nb + 2, -1):
+            for call in (abi.dag_set_input, abi.dag_set_output, abi.dag_get_output):
+                with pytest.raises(abi.DagError) as e:
+                    call(d.h, bad, host.ctypes.data)
+                assert e.value.status == abi.DAG_EINVAL
+            assert not abi.dag_device_ptr(d.h, bad)[0]
+        d.set_inputs(w.make_inputs())
+        d.run()
+        O = [n.out for n in w.nodes if n.op == "gemm"][1]
+        assert abi.dag_device_ptr(d.h, O)[0]
+    finally:
+        d.close()
